@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark: Hessian-free ray-Born frequency updates per second on GB300.
+
+One step = one full update at one frequency (smoothing, ray tracing and tables, direct
+Green's function, Born forward and residual, preconditioned back-projection, update) of
+the 1024-transducer / 512x512 workload, through the library's C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--precision P]
+  python bench.py --impl reference ...     # the FP64 CPU oracle on the machine's host cores
+
+Under torchrun each rank runs an independent replica job (its own phantom seed) on its
+own GPU: there is no data-path collective (weak scaling). Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-Born freq-updates/s at 1024 xducers, 512² grid; p50/p99 request latency"
+UNIT = "freq-updates/s"
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128
+
+
+def workload(name: str, seed: int):
+    from paper_2211_00316_gb300 import phantoms as P
+    if name == "precision_ring1024":
+        w = P.breast(1024, 512, 0.45e-3, 110e-3, np.linspace(1e5, 1.2e6, 20), seed=seed, name="ring1024_grid512_breast")
+    elif name == "fp32_ring256":
+        w = P.breast(256, 288, 0.8e-3, 110e-3, np.linspace(1e5, 1e6, 10), seed=seed, name="ring256_grid288_breast")
+    elif name == "small":
+        w = P.small_two_disc()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return w
+
+
+def describe(w) -> str:
+    g = w.geom
+    return (f"{w.name}: N={g.n_xducers} ring R={g.ring_radius*1e3:.0f} mm, {g.nx}x{g.ny} grid at "
+            f"{g.dx*1e3:.2f} mm, {len(w.freqs)} freqs {w.freqs[0]/1e6:.2f}-{w.freqs[-1]/1e6:.2f} MHz, "
+            f"{w.snr_db:.0f} dB, one update per step")
+
+
+def peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+    except OSError:
+        pass
+    return {"hbm_gbs": p.get("hbm_gbs", 6800.0), "bf16_tflops": p.get("bf16_tflops", 1900.0),
+            "bf16_tflops_sustained": p.get("bf16_tflops_sustained", 1700.0),
+            "source": "measured" if p else "fallback"}
+
+
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2211_00316_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (workload, kernel); valid only for the kernel sources they were taken on.
+NCU_TRAFFIC = {}
+
+
+def algorithmic(kernel: str, N: int, X: int, precision: str):
+    """Algorithmic work per launch of each timed kernel: (amount, unit, bound)."""
+    NX = N * X
+    if kernel == "gemm_bp":
+        return 8.0 * 2 * X * N * N, "flop", "alu" if precision == "fp32" else "tensor"
+    if kernel == "gemm_fwd":
+        return 8.0 * N * (N + 1) / 2 * X, "flop", "alu" if precision == "fp32" else "tensor"
+    if kernel == "trace":
+        return 16.0 * NX + 16.0 * N * (N - 1), "byte", "hbm"
+    if kernel == "synth_fwd":
+        return (16.0 + 8.0) * NX, "byte", "hbm"
+    if kernel == "synth_bp":
+        return (16.0 + 4.0 + 16.0) * NX, "byte", "hbm"
+    if kernel == "tables":
+        return (16.0 * 3 + 4.0) * NX, "byte", "hbm"
+    return None, None, None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, f: float) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of one update of the workload,
+    scaled to freq-updates/s. Each part runs with all host threads busy: ray fans of
+    4 x threads transducers (tables), the Born forward over all mask nodes for the
+    (2 x threads)^2 (e, r) entries of 2 x threads fans, and the unfactorised back-projection
+    at 32 x threads mask nodes; the O(N^2) direct Green's function and the update are
+    negligible beside them."""
+    from oracle import oracle as O
+    o = O.Oracle(w.geom)
+    N, X = o.N, o.X
+    rng = np.random.default_rng(0)
+    nth = O.Oracle.threads()
+    t0 = time.perf_counter()
+    ns, f6 = o.fields_for(w.c_init, f)
+    t_fields = time.perf_counter() - t0
+    nfans = min(N, 4 * nth)
+    fans = np.linspace(0, N - 1, nfans).astype(np.int32)
+    t0 = time.perf_counter()
+    tb = o.tables(f6, fans=fans)
+    t_rays = (time.perf_counter() - t0) / nfans * N
+    nr = min(nfans, 2 * nth)
+    v = rng.standard_normal(X) * 1e-3
+    t0 = time.perf_counter()
+    O.forward_rows(o, f, tb.T[:nr], tb.a[:nr], tb.K[:nr], v)
+    t_fwd = (time.perf_counter() - t0) / (nr * nr) * N * N
+    nn = 32 * nth
+    Ts, As, Gs, Ks, Ds = (rng.uniform(1e-5, 1e-4, (N, nn)), rng.uniform(1, 10, (N, nn)),
+                          rng.uniform(-3, 3, (N, nn)), np.zeros((N, nn), np.int32), rng.uniform(0, 0.01, (N, nn)))
+    R = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    t0 = time.perf_counter()
+    O.backproject_nodes(o, f, Ts, As, Gs, Ks, Ds, R)
+    t_bp = (time.perf_counter() - t0) / nn * X
+    total = t_fields + t_rays + t_fwd + t_bp
+    return {"value": 1.0 / total, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": (f"one update extrapolated from: ray fans of {nfans}/{N} transducers, Born forward of "
+                       f"{nr}x{nr}/{N}x{N} (e,r) entries over all {X} mask nodes, back-projection at {nn}/{X} "
+                       f"nodes (s per full update: rays {t_rays:.1f}, forward {t_fwd:.1f}, "
+                       f"back-projection {t_bp:.1f})"),
+            "seconds_per_update": total}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload, 0)
+    vals = []
+    t_start = time.perf_counter()
+    for k in range(args.steps):
+        f = float(w.freqs[k % len(w.freqs)])
+        cb = cpu_baseline(w, f)
+        vals.append(cb["seconds_per_update"])
+    wall = time.perf_counter() - t_start
+    value = len(vals) / sum(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": describe(w), "parallelism": "host threads"},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rbx", choices=["rbx", "reference"])
+    ap.add_argument("--workload", default="precision_ring1024", choices=["precision_ring1024", "fp32_ring256", "small"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2211_00316_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2211_00316_gb300 import phantoms as P
+    from paper_2211_00316_gb300 import rbx
+
+    prec = {"fp32": rbx.RBX_FP32, "bf16": rbx.RBX_BF16, "bf16x3": rbx.RBX_BF16X3}[args.precision]
+    w = workload(args.workload, rank)
+    g = w.geom
+    stream = torch.cuda.Stream()
+    total_steps = args.warmup + args.steps
+    with torch.cuda.stream(stream):
+        job = rbx.Job(stream)
+        job.set_geometry(g, precision=prec)
+        N, X = job.N, job.X
+        # synthetic data: the library's own ray-Born prediction on the true model + 40 dB noise
+        job.set_model(torch.tensor(w.c_true, dtype=torch.float32, device="cuda"))
+        fidx = [k % len(w.freqs) for k in range(total_steps)]
+        uniq = sorted(set(fidx))
+        data = {}
+        for q in uniq:
+            f = float(w.freqs[q])
+            job.trace_rays(f)
+            data[q] = job.predict(f).cpu().numpy()
+        noisy = P.add_noise(np.stack([data[q] for q in uniq]), w.snr_db, seed=100 + rank)
+        data_dev = {q: torch.tensor(noisy[i], dtype=torch.complex64, device="cuda") for i, q in enumerate(uniq)}
+        data_host = {q: torch.tensor(noisy[i], dtype=torch.complex64).pin_memory() for i, q in enumerate(uniq)}
+        c_init = torch.tensor(w.c_init, dtype=torch.float32, device="cuda")
+        job.set_model(c_init)
+        df = w.dfreq
+        for k in range(args.warmup):
+            job.update_frequency(float(w.freqs[fidx[k]]), df, data_dev[fidx[k]])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = Clocks(local)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        stats = []
+        for k in range(args.warmup, total_steps):
+            stats.append(job.update_frequency(float(w.freqs[fidx[k]]), df, data_dev[fidx[k]]))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        value = world * args.steps / (ms / 1e3)
+
+        # end to end through the host-buffer entry point: H2D of the step's data and D2H of the model
+        e2e = None
+        if not args.no_e2e:
+            job.set_model(c_init)
+            c_host = torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory()
+            for k in range(min(2, args.warmup)):
+                job.update_frequency_host(float(w.freqs[fidx[k]]), df, data_host[fidx[k]], c_host)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for k in range(args.warmup, total_steps):
+                job.update_frequency_host(float(w.freqs[fidx[k]]), df, data_host[fidx[k]], c_host)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            if world > 1:
+                t = torch.tensor([el], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                el = float(t.item())
+            e2e = {"value": world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": N * N * 8,
+                   "d2h_bytes_per_step": g.nx * g.ny * 4}
+        job.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # per-kernel device time averaged over the timed steps; roofline of the dominant kernel
+    kms = {k: float(np.mean([s["ms_kernel"][k] for s in stats])) for k in stats[0]["ms_kernel"]}
+    dom = max(kms, key=kms.get)
+    pk = peaks()
+    amount, unit, bound = algorithmic(dom, N, X, args.precision)
+    roof = None
+    if amount is not None:
+        dur = kms[dom] / 1e3
+        if bound == "hbm":
+            achieved, peak, u = amount / dur / 1e9, pk["hbm_gbs"], "GB/s"
+        elif bound == "tensor":
+            achieved, peak, u = amount / dur / 1e12, pk["bf16_tflops_sustained"], "TFLOP/s"
+        else:
+            achieved = amount / dur / 1e12
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            u = "TFLOP/s"
+        tr = NCU_TRAFFIC.get((args.workload, dom))
+        traffic = tr["bytes"] if tr and tr.get("src") == kernel_src_hash() else None
+        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
+                "frac": achieved / peak, "traffic": traffic, "algorithmic_per_launch": amount,
+                "peak_source": (pk["source"] if bound != "alu" else
+                                "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2070 MHz")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
+            "data": "synthetic (library ray-Born prediction on a seeded breast-like phantom + 40 dB noise)",
+            "config": {"workload": describe(w), "mask_nodes": X, "precision": args.precision,
+                       "l2": "inputs larger than L2 (tables N*X*16 B = %.2f GB)" % (16.0 * N * X / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": int(sum(s["n_launches"] for s in stats)),
+            "clocks": clk, "e2e": e2e, "roofline": roof,
+            "kernel_ms": kms, "stage_ms": {k: float(np.mean([s[k] for s in stats]))
+                                           for k in ("ms_trace", "ms_forward", "ms_backproj", "ms_total")},
+            "n_uncovered": int(stats[-1]["n_uncovered"]), "rms_dc_last": stats[-1]["rms_dc"]}
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_baseline(w, float(w.freqs[0]))
+        cb.pop("seconds_per_update", None)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * rbx.h -- C ABI of the GB300 ray-Born library: one preconditioned, Hessian-free
+ * sound-speed update per frequency (Javaherian, arXiv 2211.00316).
+ *
+ * Geometry (Sec. 2.1): a 2-D square grid of nx x ny nodes, node (ix, iy) at
+ * (x0 + ix dx, y0 + iy dx), arrays row-major [iy][ix]; N point transducers on a ring of
+ * radius R centred at the origin, transducer e at R (cos 2 pi e/N, sin 2 pi e/N), each
+ * both emitter and receiver. The reconstruction mask is |x| <= mask_radius (Sec. 6.3).
+ *
+ * Conventions shared by every call:
+ *  - Pointers named *_dev are CUDA device pointers, *_host are host pointers. The caller
+ *    owns every pointer it passes; the job owns only its internal workspaces.
+ *  - Complex arrays are interleaved (re, im) float32. Data, residual and forward outputs
+ *    are emitter-major N x N: element [e*N + r] holds g(omega, r, e) (receiver r, emitter e).
+ *  - Frequencies are in Hz; omega = 2 pi f. The time-harmonic convention is that of
+ *    Sec. 2.1 (p(omega) = int p(t) e^{+i omega t} dt): a delay T is the phase e^{+i omega T}.
+ *  - Every call is asynchronous on the job's stream except those that fill an rbx_stats
+ *    (they synchronise the stream before returning). A job is used by one host thread at a
+ *    time. No call throws; each returns an rbx_status and rbx_last_error() describes the
+ *    last failure of that job.
+ *  - There is no CPU fallback: a call that cannot run its CUDA kernels fails with
+ *    RBX_ECUDA.
+ */
+#ifndef RBX_H
+#define RBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rbx_job rbx_job;
+
+typedef enum {
+    RBX_OK = 0,
+    RBX_EINVAL = 1,    /* bad argument or geometry */
+    RBX_ENOMEM = 2,    /* device allocation failed */
+    RBX_ECUDA = 3,     /* a CUDA call or kernel failed (message in rbx_last_error) */
+    RBX_ESTATE = 4,    /* call out of order, e.g. forward before trace_rays */
+    RBX_ENUMERIC = 5,  /* non-finite input or a non-positive updated squared slowness */
+    RBX_ETIMEOUT = 6   /* a bounded device-side wait gave up */
+} rbx_status;
+
+typedef enum {
+    RBX_FP32 = 0,      /* FP32 SIMT contractions */
+    RBX_BF16 = 1,      /* BF16 tensor-core contractions, FP32 accumulation */
+    RBX_BF16X3 = 2     /* split BF16 (hi + lo, three products), FP32 accumulation */
+} rbx_precision;
+
+typedef struct {
+    int nx, ny;             /* grid nodes */
+    double dx;              /* grid spacing [m] */
+    double x0, y0;          /* position of node (0,0) [m] */
+    int n_xducers;          /* N >= 3 */
+    double ring_radius;     /* R [m]; the grid must contain the ring with one node to spare */
+    double mask_radius;     /* reconstruction mask radius [m], <= R (the paper uses 0.9 R) */
+    double c0;              /* water sound speed [m/s] */
+    double ds;              /* ray step [m] (Delta s of Def. ray-parameterisation) */
+    int weight_mode;        /* 0: scattering-angle weight as printed (Eq. btk-amp-angle);
+                               1: isochron weight |k_e + k_r| (App. D) */
+    double tau;             /* step length of m <- m + tau dm (Sec. 3.4) */
+    int precision;          /* rbx_precision of the two contractions */
+} rbx_geometry;
+
+typedef struct {
+    double resid_norm2;     /* sum over r != e of |g_pred - data|^2 */
+    double rms_dc;          /* RMS of the sound-speed change over the mask [m/s] */
+    double max_abs_dc;      /* max |dc| over the mask [m/s] */
+    double dm_norm;         /* ||dm||_2 over the mask [s^2/m^2] */
+    long long n_uncovered;  /* (transducer, mask node) entries no ray triangle covered */
+    long long n_clamped;    /* (e, r) pairs outside every exit-angle bracket */
+    long long n_launches;   /* kernels launched by this call */
+    float ms_trace;         /* smoothing, ray tracing and tables */
+    float ms_forward;       /* direct Green's function, Born forward, residual */
+    float ms_backproj;      /* back-projection and update */
+    float ms_total;
+    float ms_kernel[8];     /* per-kernel device time of the call: see RBX_K_* */
+} rbx_stats;
+
+/* indices into rbx_stats.ms_kernel */
+#define RBX_K_TRACE 0       /* ray trace + ray-to-grid scatter */
+#define RBX_K_SYNTH_FWD 1   /* Green's function synthesis for the forward */
+#define RBX_K_GEMM_FWD 2    /* Born forward contraction */
+#define RBX_K_SYNTH_BP 3    /* reciprocal Green's function synthesis */
+#define RBX_K_GEMM_BP 4     /* back-projection contraction with fused row-dot */
+#define RBX_K_FIELDS 5      /* smoothing + derivative fields */
+#define RBX_K_TABLES 6      /* table init, angular density, direct Green's function */
+#define RBX_K_UPDATE 7      /* residual + update */
+
+/* Create a job bound to a CUDA stream (a cudaStream_t; NULL means the legacy default
+ * stream). All of the job's work is queued on that stream, so it is ordered with whatever
+ * the caller queues there (e.g. the copies that fill its input buffers). The job starts
+ * without geometry. */
+rbx_status rbx_create(rbx_job **out, void *cuda_stream);
+
+/* Set the grid, ring and options (Sec. 2.1, Sec. 6.3) and allocate the job's device
+ * workspaces (tables of N x X entries, X = mask nodes). Fails with RBX_EINVAL when the
+ * grid does not contain the ring, mask_radius > ring_radius, N < 3, ds <= 0, or a ray
+ * could need more than 2047 steps (2 R / ds). Resets the model to water (c0). */
+rbx_status rbx_set_geometry(rbx_job *job, const rbx_geometry *geom);
+
+/* Number of mask nodes X and their row-major node indices (idx_dev: X int32, may be NULL). */
+rbx_status rbx_mask(rbx_job *job, int *X_out, int *idx_dev);
+
+/* Copy the sound-speed map c (ny*nx float32, m/s, device) into the job. RBX_ENUMERIC if
+ * any value is not finite and positive (checked on the device, synchronises). */
+rbx_status rbx_set_model(rbx_job *job, const float *c_dev);
+
+/* Copy the job's current sound-speed map out (ny*nx float32, device). */
+rbx_status rbx_get_model(rbx_job *job, float *c_dev);
+
+/* Steps a1-a4 on the current model for frequency f: smooth the slowness with the
+ * frequency's window (Sec. 6.2, 6.3.2), trace the ray fan of every transducer by Heun's
+ * method with the paraxial system (Alg. 1), and scatter travel time, amplitude,
+ * direction and caustic count onto the mask nodes (Sec. 4.4, Eqs. phase-discretised,
+ * amplitude-geom-discretised); then the angular density |d gamma/d e| Delta e. */
+rbx_status rbx_trace_rays(rbx_job *job, double freq_hz);
+
+/* Replace the job's tables by caller-supplied ones ([N][X] device arrays: travel time
+ * [s], reduced amplitude a [m^-1/2] (a = 0 marks an uncovered entry), direction angle
+ * [rad], caustic count) and per-ray exit records exits_dev ([N][N-1][4] float32: exit
+ * angle, T, a, K of ray j = 1..N-1). Used to run the contractions on given tables. */
+rbx_status rbx_set_tables(rbx_job *job, const float *T_dev, const float *a_dev, const float *gamma_dev,
+                          const uint8_t *K_dev, const float *exits_dev);
+
+/* Copy the job's tables out (any pointer may be NULL): [N][X] arrays as in
+ * rbx_set_tables plus dgamma ([N][X], |d gamma/d e| Delta e) and exits. */
+rbx_status rbx_get_tables(rbx_job *job, float *T_dev, float *a_dev, float *gamma_dev, uint8_t *K_dev,
+                          float *dgamma_dev, float *exits_dev);
+
+/* Direct Green's function at the receivers from the ray fans (Eq. 2D_greens, step a5):
+ * g[e*N + r] complex64, zero diagonal. */
+rbx_status rbx_direct_green(rbx_job *job, double freq_hz, void *g_dev);
+
+/* Ray-Born forward of a squared-slowness perturbation (Eqs. perturb1, derivative,
+ * scattering-potential): D[e*N + r] = omega^2 dA sum_x G_r[x] G_e[x] dm[x] over the mask,
+ * dm_dev ny*nx float32 [s^2/m^2]. Uses the tables of the last trace/set_tables. */
+rbx_status rbx_forward(rbx_job *job, double freq_hz, const float *dm_dev, void *D_dev);
+
+/* Predicted data on the current model: g_dir + F[m - m_s], m_s the smoothed squared
+ * slowness of the tables' window (diagonal zero). Also the synthetic data generator. */
+rbx_status rbx_predict(rbx_job *job, double freq_hz, void *g_dev);
+
+/* Adjoint maps of a residual R (N x N complex64, device) onto the mask nodes
+ * (out_dev: X complex64 in mask order).
+ *  preconditioned = 0: F* R = omega^2 dA sum_{e,r} conj(G_r G_e) R[e,r] (Eq. functional-gradient, Q = 1).
+ *  preconditioned = 1: sum_{e,r} W_er u_e u_r R[e,r], u_e = dgamma_e gdag_e (Eq. sound_speed_update2
+ *  without its scalar factor Delta omega m / ((2 pi)^3 omega)). */
+rbx_status rbx_adjoint(rbx_job *job, double freq_hz, const void *R_dev, void *out_dev, int preconditioned);
+
+/* One Hessian-free update at frequency f with sweep spacing df (Delta omega = 2 pi df):
+ * trace (a1-a4), direct Green's function, Born prediction and residual against data_dev
+ * (N x N complex64), preconditioned back-projection, m <- m + tau dm on the mask and
+ * c = m^-1/2 (water outside the mask). Synchronises and fills *out (may be NULL). */
+rbx_status rbx_update_frequency(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_dev, rbx_stats *out);
+
+/* Steps a5-a9 alone: one update on the job's current tables (from rbx_trace_rays or
+ * rbx_set_tables) without re-tracing; the smoothed squared slowness m_s of the Born term is
+ * recomputed from the current model with the window of freq_hz. */
+rbx_status rbx_update_from_tables(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_dev, rbx_stats *out);
+
+/* As rbx_update_frequency with host buffers: copies data_host (N x N complex64) to the
+ * device, runs the update and copies the updated model to c_out_host (ny*nx float32,
+ * may be NULL). */
+rbx_status rbx_update_frequency_host(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_host,
+                                     float *c_out_host, rbx_stats *out);
+
+/* Low-to-high frequency sweep (Sec. 3.4): one update per frequency freqs_hz[0..nf-1]
+ * (host array), data_dev holding nf consecutive N x N complex64 blocks; df of frequency n
+ * is half the distance between its neighbours (one-sided at the ends; 1 MHz / 10 when
+ * nf == 1). per_freq (host, nf entries) may be NULL. */
+rbx_status rbx_reconstruct(rbx_job *job, const double *freqs_hz, int nf, const void *data_dev, rbx_stats *per_freq);
+
+/* Last error message of the job ("" if none). The string lives as long as the job. */
+const char *rbx_last_error(const rbx_job *job);
+
+/* Wait for all work queued on the job's stream. */
+rbx_status rbx_synchronize(rbx_job *job);
+
+/* Wait for the job's stream, then free the job's device memory. */
+rbx_status rbx_destroy(rbx_job *job);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -260,3 +260,25 @@ class Oracle:
         cm = np.asarray(c, float).ravel()[self.idx]
         nm = np.asarray(ns, float).ravel()[self.idx]
         return w * w * self.geom.dx ** 2 * (1.0 / cm ** 2 - nm ** 2)
+
+
+def forward_rows(o: Oracle, f: float, T, a, K, v):
+    """og_forward restricted to the fans whose tables are the rows of [n][X] arrays:
+    returns the n x n block of D between those fans."""
+    g = OGeom.from_buffer_copy(o.g)
+    g.N = T.shape[0]
+    T, a, K, v = _f64(T), _f64(a), _i32(K), _f64(v)
+    D = np.zeros((g.N, g.N), np.complex128)
+    o.L.og_forward(C.byref(g), f, T.shape[1], _d(T), _d(a), _i(K), _d(v), _d(D.view(np.float64)))
+    return D
+
+
+def backproject_nodes(o: Oracle, f: float, T, a, gam, K, dg, R):
+    """og_backproject on tables given only at nn nodes ([N][nn] arrays): returns nn values."""
+    T, a, gam, K, dg = _f64(T), _f64(a), _f64(gam), _i32(K), _f64(dg)
+    nn = T.shape[1]
+    nodes = np.arange(nn, dtype=np.int32)
+    out = np.zeros(nn, np.complex128)
+    o.L.og_backproject(C.byref(o.g), f, nn, _d(T), _d(a), _d(gam), _i(K), _d(dg), _d(_cplx_to_f64(R)),
+                       _i(nodes), nn, _d(out.view(np.float64)))
+    return out

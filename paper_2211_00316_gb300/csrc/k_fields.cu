@@ -1,0 +1,148 @@
+// Step a1: mask map, smoothing of the slowness and its derivative fields.
+//
+// The paper traces rays on a wavenumber map smoothed by an odd moving-average window
+// whose width falls from low to high frequency (Sec. 6.2, Sec. 6.3.2) and interpolates
+// k, grad k and the Hessian of k onto the rays (Sec. 4.4). With k = omega n the ray path
+// does not depend on omega, so the fields are those of the slowness n = 1/c.
+//
+// These kernels touch the grid a few times (512^2 nodes at the largest workload) and are
+// computed in FP64: second differences of a slowness that varies by a few percent lose
+// most of their digits in FP32. The results are stored as FP32, 8 floats per node, so a
+// bilinear gather of one node reads two aligned float4.
+#include "rbx_internal.cuh"
+
+namespace rbx {
+
+// Row-major ordering of mask nodes needs a prefix count; the grid is at most a few
+// hundred thousand nodes, so a single block does it in two passes over rows.
+__global__ void k_mask_single(int nx, int ny, double dx, double x0, double y0, double r2, int *node2x, int *count)
+{
+    extern __shared__ int rowcnt[];
+    // positions and radii rounded exactly as written (no FMA contraction), so the mask
+    // is the same node set as any IEEE double evaluation of |x|^2 <= r^2
+    for (int iy = threadIdx.x; iy < ny; iy += blockDim.x) {
+        double y = __dadd_rn(y0, __dmul_rn((double)iy, dx));
+        int cnt = 0;
+        for (int ix = 0; ix < nx; ix++) {
+            double x = __dadd_rn(x0, __dmul_rn((double)ix, dx));
+            cnt += (__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)) <= r2);
+        }
+        rowcnt[iy] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int iy = 0; iy < ny; iy++) {
+            int c = rowcnt[iy];
+            rowcnt[iy] = acc;
+            acc += c;
+        }
+        *count = acc;
+    }
+    __syncthreads();
+    for (int iy = threadIdx.x; iy < ny; iy += blockDim.x) {
+        double y = __dadd_rn(y0, __dmul_rn((double)iy, dx));
+        int k = rowcnt[iy];
+        for (int ix = 0; ix < nx; ix++) {
+            double x = __dadd_rn(x0, __dmul_rn((double)ix, dx));
+            node2x[iy * nx + ix] = (__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)) <= r2) ? k++ : -1;
+        }
+    }
+}
+
+void launch_mask(const rbx_geometry &g, int *node2x, int *count, cudaStream_t s)
+{
+    k_mask_single<<<1, 256, g.ny * sizeof(int), s>>>(g.nx, g.ny, g.dx, g.x0, g.y0, g.mask_radius * g.mask_radius,
+                                                     node2x, count);
+}
+
+__global__ void k_mask_idx(const int *node2x, int nxy, int *idx)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nxy && node2x[k] >= 0) idx[node2x[k]] = k;
+}
+
+void launch_mask_idx(const int *node2x, int nxy, int *idx, cudaStream_t s)
+{
+    k_mask_idx<<<(nxy + 255) / 256, 256, 0, s>>>(node2x, nxy, idx);
+}
+
+__device__ __forceinline__ int clampi(int i, int lo, int hi) { return i < lo ? lo : (i > hi ? hi : i); }
+
+// Moving average of width w along x of the slowness 1/c (edges replicated).
+__global__ void k_smooth_x(const float *__restrict__ c, double *__restrict__ t, int nx, int ny, int w)
+{
+    int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+    if (ix >= nx) return;
+    int h = (w - 1) / 2;
+    double s = 0;
+    for (int d = -h; d <= h; d++) s += 1.0 / (double)c[iy * nx + clampi(ix + d, 0, nx - 1)];
+    t[iy * nx + ix] = s / w;
+}
+
+// Moving average along y (edges replicated).
+__global__ void k_smooth_y(const double *__restrict__ t, double *__restrict__ ns64, float *__restrict__ ns, int nx,
+                           int ny, int w)
+{
+    int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+    if (ix >= nx) return;
+    int h = (w - 1) / 2;
+    double s = 0;
+    for (int d = -h; d <= h; d++) s += t[clampi(iy + d, 0, ny - 1) * nx + ix];
+    s /= w;
+    ns64[iy * nx + ix] = s;
+    ns[iy * nx + ix] = (float)s;
+}
+
+// Central differences of the smoothed slowness (edge indices clamped).
+__global__ void k_fields(const double *__restrict__ ns, float *__restrict__ F, int nx, int ny, double dx)
+{
+    int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+    if (ix >= nx) return;
+    auto at = [&](int i, int j) { return ns[clampi(j, 0, ny - 1) * nx + clampi(i, 0, nx - 1)]; };
+    double c = at(ix, iy);
+    double fx = (at(ix + 1, iy) - at(ix - 1, iy)) / (2 * dx);
+    double fy = (at(ix, iy + 1) - at(ix, iy - 1)) / (2 * dx);
+    double fxx = (at(ix + 1, iy) - 2 * c + at(ix - 1, iy)) / (dx * dx);
+    double fxy = (at(ix + 1, iy + 1) - at(ix - 1, iy + 1) - at(ix + 1, iy - 1) + at(ix - 1, iy - 1)) / (4 * dx * dx);
+    double fyy = (at(ix, iy + 1) - 2 * c + at(ix, iy - 1)) / (dx * dx);
+    float4 *o = reinterpret_cast<float4 *>(F + (size_t)(iy * nx + ix) * kFieldStride);
+    o[0] = make_float4((float)c, (float)fx, (float)fy, (float)fxx);
+    o[1] = make_float4((float)fxy, (float)fyy, 0.f, 0.f);
+}
+
+void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *tmp64, double *ns64, float *ns,
+                          float *fields, cudaStream_t s)
+{
+    dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
+    k_smooth_x<<<grd, blk, 0, s>>>(c, tmp64, g.nx, g.ny, w);
+    k_smooth_y<<<grd, blk, 0, s>>>(tmp64, ns64, ns, g.nx, g.ny, w);
+    k_fields<<<grd, blk, 0, s>>>(ns64, fields, g.nx, g.ny, g.dx);
+}
+
+__global__ void k_check_model(const float *c, int n, unsigned long long *flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float v = c[i];
+        if (!(v > 0.f) || !isfinite(v)) atomicAdd(flag, 1ull);
+    }
+}
+
+void launch_check_model(const float *c, int n, unsigned long long *flag, cudaStream_t s)
+{
+    k_check_model<<<(n + 255) / 256, 256, 0, s>>>(c, n, flag);
+}
+
+__global__ void k_fill(float *p, float v, size_t n)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+void launch_fill(float *p, float v, size_t n, cudaStream_t s)
+{
+    k_fill<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, v, n);
+}
+
+}  // namespace rbx

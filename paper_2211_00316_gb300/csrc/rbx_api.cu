@@ -1,0 +1,540 @@
+// C ABI of the rbx library: job state, argument checks and the order of the steps of one
+// Hessian-free update (declared in include/rbx.h).
+#include "rbx_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <string>
+
+using namespace rbx;
+
+namespace rbx {
+void launch_add_offdiag(const float2 *a, const float2 *b, int N, float2 *out, cudaStream_t s);
+}
+
+enum { EV_START, EV_FIELDS, EV_TRACE, EV_TABLES, EV_GDIR, EV_SYNTH_F, EV_GEMM_F, EV_RESID, EV_SYNTH_B, EV_GEMM_B,
+       EV_UPDATE, EV_COUNT };
+
+struct rbx_job {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    rbx_geometry g{};
+    bool has_geom = false, has_tables = false, ns_valid = false;
+    int ns_window = 0;
+    Workspace w;
+    int *d_count = nullptr;
+    std::string err;
+    cudaEvent_t ev[EV_COUNT]{};
+    long long launches = 0;
+};
+
+static rbx_status fail(rbx_job *j, rbx_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (j) j->err = buf;
+    return st;
+}
+
+#define CUDA_TRY(job, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(job, RBX_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+#define LAUNCHED(job, n)                                                                     \
+    do {                                                                                     \
+        (job)->launches += (n);                                                              \
+        CUDA_TRY(job, cudaGetLastError());                                                   \
+    } while (0)
+#define NEED(job, cond, st, msg)                                                             \
+    do {                                                                                     \
+        if (!(cond)) return fail(job, st, "%s", msg);                                        \
+    } while (0)
+
+template <class T>
+static cudaError_t dalloc(T *&p, size_t n)
+{
+    return cudaMalloc(reinterpret_cast<void **>(&p), (n ? n : 1) * sizeof(T));
+}
+
+static void free_ws(Workspace &w)
+{
+    void *ps[] = {w.node2x, w.idx, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
+                  w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    w = Workspace{};
+}
+
+// Odd smoothing window in grid points: 13, 11, 9, 7 on a 1 mm grid below 0.4, 0.7, 1 MHz
+// and above; scaled by (1 mm / dx) to the nearest odd integer (Sec. 6.2, Sec. 6.3.2).
+static int window_for(double f, double dx)
+{
+    double w1 = f < 0.4e6 ? 13.0 : (f < 0.7e6 ? 11.0 : (f < 1.0e6 ? 9.0 : 7.0));
+    double w = w1 * (1e-3 / dx);
+    int k = (int)std::floor((w - 1.0) / 2.0 + 0.5);
+    if (k < 0) k = 0;
+    return 2 * k + 1;
+}
+
+static int max_steps(const rbx_geometry &g) { return (int)std::ceil(3.0 * g.ring_radius / g.ds) + 8; }
+
+static float elapsed(const rbx_job *j, int a, int b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, j->ev[a], j->ev[b]) != cudaSuccess) return 0.f;
+    return ms;
+}
+
+static rbx_status record(rbx_job *j, int k)
+{
+    CUDA_TRY(j, cudaEventRecord(j->ev[k], j->stream));
+    return RBX_OK;
+}
+
+extern "C" {
+
+rbx_status rbx_create(rbx_job **out, void *cuda_stream)
+{
+    if (!out) return RBX_EINVAL;
+    *out = nullptr;
+    rbx_job *j = new (std::nothrow) rbx_job();
+    if (!j) return RBX_ENOMEM;
+    j->stream = static_cast<cudaStream_t>(cuda_stream);   // NULL: the legacy default stream
+    for (int k = 0; k < EV_COUNT; k++) {
+        if (cudaEventCreate(&j->ev[k]) != cudaSuccess) {
+            rbx_destroy(j);
+            return RBX_ECUDA;
+        }
+    }
+    *out = j;
+    return RBX_OK;
+}
+
+rbx_status rbx_destroy(rbx_job *j)
+{
+    if (!j) return RBX_EINVAL;
+    cudaStreamSynchronize(j->stream);
+    free_ws(j->w);
+    if (j->d_count) cudaFree(j->d_count);
+    for (int k = 0; k < EV_COUNT; k++)
+        if (j->ev[k]) cudaEventDestroy(j->ev[k]);
+    if (j->own_stream) cudaStreamDestroy(j->stream);
+    delete j;
+    return RBX_OK;
+}
+
+const char *rbx_last_error(const rbx_job *j) { return j ? j->err.c_str() : "null job"; }
+
+rbx_status rbx_synchronize(rbx_job *j)
+{
+    if (!j) return RBX_EINVAL;
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    return RBX_OK;
+}
+
+rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
+{
+    if (!j || !geom) return RBX_EINVAL;
+    const rbx_geometry &g = *geom;
+    NEED(j, g.nx >= 4 && g.ny >= 4 && std::isfinite(g.dx) && g.dx > 0, RBX_EINVAL, "grid must be >= 4x4 with dx > 0");
+    NEED(j, g.n_xducers >= 3 && g.n_xducers <= kMaxXducers, RBX_EINVAL, "n_xducers must be in [3, 4095]");
+    NEED(j, std::isfinite(g.ring_radius) && g.ring_radius > 0, RBX_EINVAL, "ring_radius must be > 0");
+    NEED(j, g.mask_radius > 0 && g.mask_radius <= g.ring_radius, RBX_EINVAL, "mask_radius must be in (0, R]");
+    NEED(j, std::isfinite(g.c0) && g.c0 > 0, RBX_EINVAL, "c0 must be > 0");
+    NEED(j, std::isfinite(g.ds) && g.ds > 0, RBX_EINVAL, "ds must be > 0");
+    NEED(j, g.weight_mode == 0 || g.weight_mode == 1, RBX_EINVAL, "weight_mode must be 0 or 1");
+    NEED(j, std::isfinite(g.tau), RBX_EINVAL, "tau must be finite");
+    NEED(j, g.precision >= 0 && g.precision <= 2, RBX_EINVAL, "precision must be 0, 1 or 2");
+    double xl = g.x0, xr = g.x0 + (g.nx - 1) * g.dx, yl = g.y0, yr = g.y0 + (g.ny - 1) * g.dx;
+    NEED(j, xl <= -g.ring_radius - g.dx && xr >= g.ring_radius + g.dx && yl <= -g.ring_radius - g.dx &&
+                yr >= g.ring_radius + g.dx,
+         RBX_EINVAL, "the grid must contain the ring with one node to spare");
+    NEED(j, max_steps(g) <= kMaxSteps, RBX_EINVAL, "ring_radius / ds too large (rays limited to 2047 steps)");
+    NEED(j, (double)g.nx * g.ny < 2e9, RBX_EINVAL, "grid too large");
+
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    free_ws(j->w);
+    j->has_geom = j->has_tables = j->ns_valid = false;
+    Workspace &w = j->w;
+    w.N = g.n_xducers;
+    w.nx = g.nx;
+    w.ny = g.ny;
+    const size_t nxy = (size_t)g.nx * g.ny, N = w.N;
+    if (!j->d_count) CUDA_TRY(j, dalloc(j->d_count, 1));
+#define ALLOC(p, n)                                                                                   \
+    do {                                                                                              \
+        if (dalloc(p, n) != cudaSuccess) {                                                            \
+            cudaGetLastError();                                                                       \
+            free_ws(w);                                                                               \
+            return fail(j, RBX_ENOMEM, "device allocation of %s (%zu elements) failed", #p, (size_t)(n)); \
+        }                                                                                             \
+    } while (0)
+    ALLOC(w.node2x, nxy);
+    launch_mask(g, w.node2x, j->d_count, j->stream);
+    LAUNCHED(j, 1);
+    int X = 0;
+    CUDA_TRY(j, cudaMemcpyAsync(&X, j->d_count, sizeof(int), cudaMemcpyDeviceToHost, j->stream));
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    NEED(j, X > 0, RBX_EINVAL, "the mask contains no grid node");
+    w.X = X;
+    w.fwd_splits = forward_splits(w.N, X);
+    const size_t NX = N * (size_t)X;
+    ALLOC(w.idx, X);
+    ALLOC(w.c, nxy);
+    ALLOC(w.ns, nxy);
+    ALLOC(w.ns64, nxy);
+    ALLOC(w.tmp64, nxy);
+    ALLOC(w.fields, nxy * kFieldStride);
+    ALLOC(w.tab, NX);
+    ALLOC(w.dg, NX);
+    ALLOC(w.exits, N * (N - 1));
+    ALLOC(w.G, NX);
+    ALLOC(w.U, NX);
+    ALLOC(w.kap, NX);
+    ALLOC(w.v, X);
+    ALLOC(w.gdir, N * N);
+    ALLOC(w.D, N * N);
+    ALLOC(w.R, N * N);
+    ALLOC(w.Rs, N * N);
+    ALLOC(w.data, N * N);
+    ALLOC(w.part, (size_t)w.fwd_splits * N * N);
+    ALLOC(w.gpart, 2 * (size_t)X);
+    size_t nred = (size_t)residual_blocks(w.N) + 8;
+    size_t nred2 = 3 * (size_t)update_blocks(g.nx, g.ny) + 8;
+    ALLOC(w.red, nred > nred2 ? nred : nred2);
+    ALLOC(w.counters, 8);
+#undef ALLOC
+    launch_mask_idx(w.node2x, (int)nxy, w.idx, j->stream);
+    launch_fill(w.c, (float)g.c0, nxy, j->stream);
+    LAUNCHED(j, 2);
+    CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 8 * sizeof(unsigned long long), j->stream));
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    j->g = g;
+    j->has_geom = true;
+    return RBX_OK;
+}
+
+rbx_status rbx_mask(rbx_job *j, int *X_out, int *idx_dev)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_mask before rbx_set_geometry");
+    if (X_out) *X_out = j->w.X;
+    if (idx_dev)
+        CUDA_TRY(j, cudaMemcpyAsync(idx_dev, j->w.idx, sizeof(int) * j->w.X, cudaMemcpyDeviceToDevice, j->stream));
+    return RBX_OK;
+}
+
+rbx_status rbx_set_model(rbx_job *j, const float *c_dev)
+{
+    if (!j || !c_dev) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_set_model before rbx_set_geometry");
+    size_t nxy = (size_t)j->w.nx * j->w.ny;
+    CUDA_TRY(j, cudaMemcpyAsync(j->w.c, c_dev, nxy * sizeof(float), cudaMemcpyDeviceToDevice, j->stream));
+    CUDA_TRY(j, cudaMemsetAsync(j->w.counters + 5, 0, sizeof(unsigned long long), j->stream));
+    launch_check_model(j->w.c, (int)nxy, j->w.counters + 5, j->stream);
+    LAUNCHED(j, 1);
+    unsigned long long bad = 0;
+    CUDA_TRY(j, cudaMemcpyAsync(&bad, j->w.counters + 5, sizeof bad, cudaMemcpyDeviceToHost, j->stream));
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    j->ns_valid = false;
+    NEED(j, bad == 0, RBX_ENUMERIC, "sound speed must be finite and positive everywhere");
+    return RBX_OK;
+}
+
+rbx_status rbx_get_model(rbx_job *j, float *c_dev)
+{
+    if (!j || !c_dev) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_get_model before rbx_set_geometry");
+    size_t nxy = (size_t)j->w.nx * j->w.ny;
+    CUDA_TRY(j, cudaMemcpyAsync(c_dev, j->w.c, nxy * sizeof(float), cudaMemcpyDeviceToDevice, j->stream));
+    return RBX_OK;
+}
+
+static rbx_status smooth(rbx_job *j, double f)
+{
+    int w = window_for(f, j->g.dx);
+    if (j->ns_valid && j->ns_window == w) return RBX_OK;
+    launch_smooth_fields(j->g, j->w.c, w, j->w.tmp64, j->w.ns64, j->w.ns, j->w.fields, j->stream);
+    LAUNCHED(j, 3);
+    j->ns_valid = true;
+    j->ns_window = w;
+    return RBX_OK;
+}
+
+static bool bad_freq(double f) { return !(std::isfinite(f) && f > 0); }
+
+rbx_status rbx_trace_rays(rbx_job *j, double f)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_trace_rays before rbx_set_geometry");
+    NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
+    Workspace &w = j->w;
+    rbx_status st;
+    if ((st = record(j, EV_START))) return st;
+    j->ns_valid = false;   // recompute the fields for this model
+    if ((st = smooth(j, f))) return st;
+    if ((st = record(j, EV_FIELDS))) return st;
+    CUDA_TRY(j, cudaMemsetAsync(w.tab, 0xff, sizeof(TabEntry) * (size_t)w.N * w.X, j->stream));
+    CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
+    RayParams p;
+    p.N = w.N; p.X = w.X; p.nx = w.nx; p.ny = w.ny;
+    p.dx = (float)j->g.dx; p.x0 = (float)j->g.x0; p.y0 = (float)j->g.y0;
+    p.R = (float)j->g.ring_radius; p.ds = (float)j->g.ds;
+    p.maxs = max_steps(j->g);
+    launch_trace_raster(w.fields, w.node2x, w.tab, w.exits, p, w.counters, j->stream);
+    LAUNCHED(j, 1);
+    if ((st = record(j, EV_TRACE))) return st;
+    launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
+    LAUNCHED(j, 1);
+    if ((st = record(j, EV_TABLES))) return st;
+    j->has_tables = true;
+    return RBX_OK;
+}
+
+rbx_status rbx_set_tables(rbx_job *j, const float *T, const float *a, const float *gam, const uint8_t *K,
+                          const float *exits)
+{
+    if (!j || !T || !a || !gam || !K || !exits) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_set_tables before rbx_set_geometry");
+    Workspace &w = j->w;
+    size_t n = (size_t)w.N * w.X;
+    launch_set_tables(T, a, gam, K, w.tab, n, j->stream);
+    CUDA_TRY(j, cudaMemcpyAsync(w.exits, exits, sizeof(float4) * (size_t)w.N * (w.N - 1), cudaMemcpyDeviceToDevice,
+                                j->stream));
+    CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
+    launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
+    LAUNCHED(j, 2);
+    j->has_tables = true;
+    return RBX_OK;
+}
+
+rbx_status rbx_get_tables(rbx_job *j, float *T, float *a, float *gam, uint8_t *K, float *dg, float *exits)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_tables, RBX_ESTATE, "rbx_get_tables before rbx_trace_rays or rbx_set_tables");
+    Workspace &w = j->w;
+    size_t n = (size_t)w.N * w.X;
+    if (T || a || gam || K) {
+        launch_get_tables(w.tab, T, a, gam, K, n, j->stream);
+        LAUNCHED(j, 1);
+    }
+    if (dg) CUDA_TRY(j, cudaMemcpyAsync(dg, w.dg, sizeof(float) * n, cudaMemcpyDeviceToDevice, j->stream));
+    if (exits)
+        CUDA_TRY(j, cudaMemcpyAsync(exits, w.exits, sizeof(float4) * (size_t)w.N * (w.N - 1), cudaMemcpyDeviceToDevice,
+                                    j->stream));
+    return RBX_OK;
+}
+
+rbx_status rbx_direct_green(rbx_job *j, double f, void *g_dev)
+{
+    if (!j || !g_dev) return RBX_EINVAL;
+    NEED(j, j->has_tables, RBX_ESTATE, "rbx_direct_green before rbx_trace_rays or rbx_set_tables");
+    NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
+    launch_direct_green(j->w.exits, j->w.N, f, j->g.c0, static_cast<float2 *>(g_dev), j->w.counters, j->stream);
+    LAUNCHED(j, 1);
+    return RBX_OK;
+}
+
+// D = sum_x G_r G_e v on the current tables, into w.D (symmetric).
+static rbx_status forward_core(rbx_job *j, double f, bool timed)
+{
+    Workspace &w = j->w;
+    rbx_status st;
+    launch_synth_fwd(w.tab, w.N, w.X, f, j->g.c0, w.G, j->stream);
+    LAUNCHED(j, 1);
+    if (timed && (st = record(j, EV_SYNTH_F))) return st;
+    launch_forward_simt(w.G, w.v, w.N, w.X, w.fwd_splits, w.part, j->stream);
+    launch_forward_reduce(w.part, w.N, w.fwd_splits, w.D, j->stream);
+    LAUNCHED(j, 2);
+    if (timed && (st = record(j, EV_GEMM_F))) return st;
+    return RBX_OK;
+}
+
+rbx_status rbx_forward(rbx_job *j, double f, const float *dm_dev, void *D_dev)
+{
+    if (!j || !dm_dev || !D_dev) return RBX_EINVAL;
+    NEED(j, j->has_tables, RBX_ESTATE, "rbx_forward before rbx_trace_rays or rbx_set_tables");
+    NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
+    Workspace &w = j->w;
+    launch_born_weights_dm(dm_dev, w.idx, w.X, f, j->g.dx * j->g.dx, w.v, j->stream);
+    LAUNCHED(j, 1);
+    rbx_status st = forward_core(j, f, false);
+    if (st) return st;
+    CUDA_TRY(j, cudaMemcpyAsync(D_dev, w.D, sizeof(float2) * (size_t)w.N * w.N, cudaMemcpyDeviceToDevice, j->stream));
+    return RBX_OK;
+}
+
+rbx_status rbx_predict(rbx_job *j, double f, void *g_dev)
+{
+    if (!j || !g_dev) return RBX_EINVAL;
+    NEED(j, j->has_tables, RBX_ESTATE, "rbx_predict before rbx_trace_rays or rbx_set_tables");
+    NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
+    Workspace &w = j->w;
+    rbx_status st;
+    if ((st = smooth(j, f))) return st;
+    launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
+    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, w.v, j->stream);
+    LAUNCHED(j, 2);
+    if ((st = forward_core(j, f, false))) return st;
+    launch_add_offdiag(w.gdir, w.D, w.N, static_cast<float2 *>(g_dev), j->stream);
+    LAUNCHED(j, 1);
+    return RBX_OK;
+}
+
+rbx_status rbx_adjoint(rbx_job *j, double f, const void *R_dev, void *out_dev, int preconditioned)
+{
+    if (!j || !R_dev || !out_dev) return RBX_EINVAL;
+    NEED(j, j->has_tables, RBX_ESTATE, "rbx_adjoint before rbx_trace_rays or rbx_set_tables");
+    NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
+    Workspace &w = j->w;
+    launch_symmetrize(static_cast<const float2 *>(R_dev), w.N, w.Rs, j->stream);
+    LAUNCHED(j, 1);
+    if (preconditioned) {
+        launch_synth_bp(w.tab, w.dg, w.N, w.X, f, j->g.c0, w.U, w.kap, j->stream);
+        launch_backproject_simt(w.U, w.kap, w.Rs, w.N, w.X, 0, w.gpart, j->stream);
+        launch_combine_adjoint(w.gpart, w.X, 0, j->g.weight_mode, 2.0, static_cast<float2 *>(out_dev), j->stream);
+    } else {
+        double om = 2 * 3.14159265358979323846 * f;
+        launch_synth_fwd(w.tab, w.N, w.X, f, j->g.c0, w.G, j->stream);
+        launch_backproject_simt(w.G, nullptr, w.Rs, w.N, w.X, 1, w.gpart, j->stream);
+        launch_combine_adjoint(w.gpart, w.X, 1, j->g.weight_mode, om * om * j->g.dx * j->g.dx,
+                               static_cast<float2 *>(out_dev), j->stream);
+    }
+    LAUNCHED(j, 3);
+    return RBX_OK;
+}
+
+static rbx_status update_core(rbx_job *j, double f, double df, const float2 *data, rbx_stats *out, bool traced)
+{
+    Workspace &w = j->w;
+    rbx_status st;
+    if (!traced && (st = record(j, EV_TABLES))) return st;
+    if ((st = smooth(j, f))) return st;
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 1, 0, sizeof(unsigned long long), j->stream));
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 4, 0, sizeof(unsigned long long), j->stream));
+    launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
+    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, w.v, j->stream);
+    LAUNCHED(j, 2);
+    if ((st = record(j, EV_GDIR))) return st;
+    if ((st = forward_core(j, f, true))) return st;
+    launch_residual(w.gdir, w.D, data, w.N, nullptr, w.Rs, w.red, j->stream);
+    LAUNCHED(j, 2);
+    double r2 = 0;
+    CUDA_TRY(j, cudaMemcpyAsync(&r2, w.red + residual_blocks(w.N), sizeof r2, cudaMemcpyDeviceToHost, j->stream));
+    if ((st = record(j, EV_RESID))) return st;
+    launch_synth_bp(w.tab, w.dg, w.N, w.X, f, j->g.c0, w.U, w.kap, j->stream);
+    LAUNCHED(j, 1);
+    if ((st = record(j, EV_SYNTH_B))) return st;
+    launch_backproject_simt(w.U, w.kap, w.Rs, w.N, w.X, 0, w.gpart, j->stream);
+    LAUNCHED(j, 1);
+    if ((st = record(j, EV_GEMM_B))) return st;
+    launch_update(w.gpart, w.node2x, w.nx, w.ny, w.X, j->g.weight_mode, f, df, j->g.tau, j->g.c0, w.c, w.red,
+                  w.counters, j->stream);
+    LAUNCHED(j, 2);
+    if ((st = record(j, EV_UPDATE))) return st;
+    j->ns_valid = false;   // the model changed
+    int nb = update_blocks(w.nx, w.ny);
+    double tot[3];
+    unsigned long long cnt[8];
+    CUDA_TRY(j, cudaMemcpyAsync(tot, w.red + 3 * nb, sizeof tot, cudaMemcpyDeviceToHost, j->stream));
+    CUDA_TRY(j, cudaMemcpyAsync(cnt, w.counters, sizeof cnt, cudaMemcpyDeviceToHost, j->stream));
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    if (out) {
+        std::memset(out, 0, sizeof *out);
+        out->resid_norm2 = r2;
+        out->rms_dc = std::sqrt(tot[0] / w.X);
+        out->max_abs_dc = tot[1];
+        out->dm_norm = std::sqrt(tot[2]);
+        out->n_uncovered = (long long)cnt[0];
+        out->n_clamped = (long long)cnt[1];
+        out->n_launches = j->launches;
+        int t0 = traced ? EV_START : EV_TABLES;
+        out->ms_trace = traced ? elapsed(j, EV_START, EV_TABLES) : 0.f;
+        out->ms_forward = elapsed(j, EV_TABLES, EV_RESID);
+        out->ms_backproj = elapsed(j, EV_RESID, EV_UPDATE);
+        out->ms_total = elapsed(j, t0, EV_UPDATE);
+        if (traced) {
+            out->ms_kernel[RBX_K_FIELDS] = elapsed(j, EV_START, EV_FIELDS);
+            out->ms_kernel[RBX_K_TRACE] = elapsed(j, EV_FIELDS, EV_TRACE);
+        }
+        out->ms_kernel[RBX_K_TABLES] = (traced ? elapsed(j, EV_TRACE, EV_TABLES) : 0.f) + elapsed(j, EV_TABLES, EV_GDIR);
+        out->ms_kernel[RBX_K_SYNTH_FWD] = elapsed(j, EV_GDIR, EV_SYNTH_F);
+        out->ms_kernel[RBX_K_GEMM_FWD] = elapsed(j, EV_SYNTH_F, EV_GEMM_F);
+        out->ms_kernel[RBX_K_SYNTH_BP] = elapsed(j, EV_RESID, EV_SYNTH_B);
+        out->ms_kernel[RBX_K_GEMM_BP] = elapsed(j, EV_SYNTH_B, EV_GEMM_B);
+        out->ms_kernel[RBX_K_UPDATE] = elapsed(j, EV_GEMM_F, EV_RESID) + elapsed(j, EV_GEMM_B, EV_UPDATE);
+    }
+    NEED(j, cnt[4] == 0, RBX_ENUMERIC, "non-finite or non-positive updated squared slowness");
+    NEED(j, cnt[2] == 0, RBX_ENUMERIC, "a ray did not reach the ring within the step limit");
+    NEED(j, cnt[3] == 0, RBX_ECUDA, "table compare-and-swap exceeded its iteration bound");
+    return RBX_OK;
+}
+
+rbx_status rbx_update_from_tables(rbx_job *j, double f, double df, const void *data_dev, rbx_stats *out)
+{
+    if (!j || !data_dev) return RBX_EINVAL;
+    NEED(j, j->has_tables, RBX_ESTATE, "rbx_update_from_tables before rbx_trace_rays or rbx_set_tables");
+    NEED(j, !bad_freq(f) && std::isfinite(df) && df > 0, RBX_EINVAL, "frequency and spacing must be finite and > 0");
+    long long l0 = j->launches;
+    rbx_status st = update_core(j, f, df, static_cast<const float2 *>(data_dev), out, false);
+    if (out) out->n_launches = j->launches - l0;
+    return st;
+}
+
+rbx_status rbx_update_frequency(rbx_job *j, double f, double df, const void *data_dev, rbx_stats *out)
+{
+    if (!j || !data_dev) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_update_frequency before rbx_set_geometry");
+    NEED(j, !bad_freq(f) && std::isfinite(df) && df > 0, RBX_EINVAL, "frequency and spacing must be finite and > 0");
+    long long l0 = j->launches;
+    rbx_status st = rbx_trace_rays(j, f);
+    if (st) return st;
+    st = update_core(j, f, df, static_cast<const float2 *>(data_dev), out, true);
+    if (out) out->n_launches = j->launches - l0;
+    return st;
+}
+
+rbx_status rbx_update_frequency_host(rbx_job *j, double f, double df, const void *data_host, float *c_out_host,
+                                     rbx_stats *out)
+{
+    if (!j || !data_host) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_update_frequency_host before rbx_set_geometry");
+    size_t nn = (size_t)j->w.N * j->w.N;
+    CUDA_TRY(j, cudaMemcpyAsync(j->w.data, data_host, sizeof(float2) * nn, cudaMemcpyHostToDevice, j->stream));
+    rbx_status st = rbx_update_frequency(j, f, df, j->w.data, out);
+    if (st) return st;
+    if (c_out_host) {
+        size_t nxy = (size_t)j->w.nx * j->w.ny;
+        CUDA_TRY(j, cudaMemcpyAsync(c_out_host, j->w.c, sizeof(float) * nxy, cudaMemcpyDeviceToHost, j->stream));
+        CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    }
+    return RBX_OK;
+}
+
+rbx_status rbx_reconstruct(rbx_job *j, const double *freqs, int nf, const void *data_dev, rbx_stats *per_freq)
+{
+    if (!j || !freqs || nf < 1 || !data_dev) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_reconstruct before rbx_set_geometry");
+    size_t nn = (size_t)j->w.N * j->w.N;
+    for (int n = 0; n < nf; n++) {
+        double df;
+        if (nf == 1) df = 1e5;
+        else if (n == 0) df = freqs[1] - freqs[0];
+        else if (n == nf - 1) df = freqs[nf - 1] - freqs[nf - 2];
+        else df = 0.5 * (freqs[n + 1] - freqs[n - 1]);
+        NEED(j, std::isfinite(df) && df > 0, RBX_EINVAL, "frequencies must increase");
+        const float2 *d = static_cast<const float2 *>(data_dev) + (size_t)n * nn;
+        rbx_status st = rbx_update_frequency(j, freqs[n], df, d, per_freq ? &per_freq[n] : nullptr);
+        if (st) return st;
+    }
+    return RBX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations of the rbx CUDA library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include "../../include/rbx.h"
+
+namespace rbx {
+
+constexpr int kFieldStride = 8;          // floats per node: n, n_x, n_y, n_xx, n_xy, n_yy, 0, 0
+constexpr uint32_t kUncovered = 0xFFFFFFFFu;
+constexpr int kMaxSteps = 2047;          // ray samples index i < 2048 (11 bits of the key)
+constexpr int kMaxXducers = 4095;        // ray index j < 4096 (12 bits of the key)
+
+// One (transducer, mask node) table entry, 16 bytes. The first 8 bytes, read as a
+// little-endian u64, are the ordering key (T bits, triangle id, K): the rasteriser keeps
+// the smallest key per node with a 128-bit compare-and-swap.
+struct __align__(16) TabEntry {
+    uint32_t idk;   // (triangle id << 8) | K ; kUncovered when no triangle covered the node
+    float T;        // travel time [s]
+    float a;        // reduced amplitude [m^-1/2]
+    float gam;      // ray direction angle [rad]
+};
+
+struct RayParams {
+    int N, X, nx, ny;
+    float dx, x0, y0, R, ds;
+    int maxs;
+};
+
+// Device workspace of one job.
+struct Workspace {
+    int N = 0, X = 0, nx = 0, ny = 0;
+    int *node2x = nullptr, *idx = nullptr;
+    float *c = nullptr, *ns = nullptr, *tmp = nullptr, *fields = nullptr;
+    double *ns64 = nullptr, *tmp64 = nullptr;
+    TabEntry *tab = nullptr;
+    float *dg = nullptr;
+    float4 *exits = nullptr;
+    float2 *G = nullptr, *U = nullptr, *kap = nullptr;
+    float *v = nullptr;
+    float2 *gdir = nullptr, *D = nullptr, *R = nullptr, *Rs = nullptr, *part = nullptr, *gpart = nullptr;
+    float2 *data = nullptr;
+    double *red = nullptr;           // reduction scratch
+    unsigned long long *counters = nullptr;   // [0] uncovered [1] clamped [2] bad rays [3] CAS bound [4] m <= 0 [5] bad model [6] mask count
+    int fwd_splits = 1;
+};
+
+// ---------------------------------------------------------------- kernels (launchers)
+// k_fields.cu
+void launch_mask(const rbx_geometry &g, int *node2x, int *count, cudaStream_t s);
+void launch_mask_idx(const int *node2x, int nxy, int *idx, cudaStream_t s);
+void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *tmp64, double *ns64, float *ns,
+                          float *fields, cudaStream_t s);
+void launch_check_model(const float *c, int n, unsigned long long *flag, cudaStream_t s);
+void launch_fill(float *p, float v, size_t n, cudaStream_t s);
+
+// k_rays.cu
+void launch_trace_raster(const float *fields, const int *node2x, TabEntry *tab, float4 *exits, const RayParams &p,
+                         unsigned long long *counters, cudaStream_t s);
+void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, unsigned long long *counters, cudaStream_t s);
+void launch_direct_green(const float4 *exits, int N, double f, double c0, float2 *g, unsigned long long *counters,
+                         cudaStream_t s);
+void launch_set_tables(const float *T, const float *a, const float *gam, const uint8_t *K, TabEntry *tab, size_t n,
+                       cudaStream_t s);
+void launch_get_tables(const TabEntry *tab, float *T, float *a, float *gam, uint8_t *K, size_t n, cudaStream_t s);
+
+// k_gemm_simt.cu
+void launch_synth_fwd(const TabEntry *tab, int N, int X, double f, double c0, float2 *G, cudaStream_t s);
+void launch_synth_bp(const TabEntry *tab, const float *dg, int N, int X, double f, double c0, float2 *U,
+                     float2 *kap, cudaStream_t s);
+void launch_born_weights_rough(const float *c, const double *ns64, const int *idx, int X, double f, double dA,
+                               float *v, cudaStream_t s);
+void launch_born_weights_dm(const float *dm, const int *idx, int X, double f, double dA, float *v, cudaStream_t s);
+int forward_splits(int N, int X);
+void launch_forward_simt(const float2 *G, const float *v, int N, int X, int splits, float2 *part, cudaStream_t s);
+void launch_forward_reduce(const float2 *part, int N, int splits, float2 *D, cudaStream_t s);
+// mode 0: preconditioned (A = U, conj(kap) U; W = U, kap U); mode 1: plain adjoint (A = W = conj(G))
+void launch_backproject_simt(const float2 *A, const float2 *kap, const float2 *Rs, int N, int X, int mode,
+                             float2 *gpart, cudaStream_t s);
+
+// k_update.cu
+void launch_residual(const float2 *gdir, const float2 *D, const float2 *data, int N, float2 *R, float2 *Rs,
+                     double *red, cudaStream_t s);
+void launch_symmetrize(const float2 *R, int N, float2 *Rs, cudaStream_t s);
+void launch_combine_adjoint(const float2 *gpart, int X, int mode, int weight_mode, double scale, float2 *out,
+                            cudaStream_t s);
+void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X, int weight_mode, double f,
+                   double df, double tau, double c0, float *c, double *red, unsigned long long *counters,
+                   cudaStream_t s);
+int residual_blocks(int N);
+int update_blocks(int nx, int ny);
+
+}  // namespace rbx

@@ -1,0 +1,229 @@
+"""Thin Python binding of librbx (include/rbx.h): argument marshalling only.
+
+Every step of the update runs in the library's CUDA kernels; this module only passes
+device pointers of torch tensors (PyTorch provides device memory and streams) and
+host scalars. It raises if the compiled library is missing: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "_build", "librbx.so")
+
+RBX_FP32, RBX_BF16, RBX_BF16X3 = 0, 1, 2
+STATUS = {0: "RBX_OK", 1: "RBX_EINVAL", 2: "RBX_ENOMEM", 3: "RBX_ECUDA", 4: "RBX_ESTATE", 5: "RBX_ENUMERIC",
+          6: "RBX_ETIMEOUT"}
+KERNELS = ["trace", "synth_fwd", "gemm_fwd", "synth_bp", "gemm_bp", "fields", "tables", "update"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RbxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Geometry(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("x0", C.c_double), ("y0", C.c_double),
+                ("n_xducers", C.c_int), ("ring_radius", C.c_double), ("mask_radius", C.c_double),
+                ("c0", C.c_double), ("ds", C.c_double), ("weight_mode", C.c_int), ("tau", C.c_double),
+                ("precision", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("resid_norm2", C.c_double), ("rms_dc", C.c_double), ("max_abs_dc", C.c_double),
+                ("dm_norm", C.c_double), ("n_uncovered", C.c_longlong), ("n_clamped", C.c_longlong),
+                ("n_launches", C.c_longlong), ("ms_trace", C.c_float), ("ms_forward", C.c_float),
+                ("ms_backproj", C.c_float), ("ms_total", C.c_float), ("ms_kernel", C.c_float * 8)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_kernel"}
+        d["ms_kernel"] = dict(zip(KERNELS, list(self.ms_kernel)))
+        return d
+
+
+_P = C.c_void_p
+_J = C.c_void_p
+_SIGS = {
+    "rbx_create": [C.POINTER(C.c_void_p), _P],
+    "rbx_set_geometry": [_J, C.POINTER(Geometry)],
+    "rbx_mask": [_J, C.POINTER(C.c_int), _P],
+    "rbx_set_model": [_J, _P],
+    "rbx_get_model": [_J, _P],
+    "rbx_trace_rays": [_J, C.c_double],
+    "rbx_set_tables": [_J, _P, _P, _P, _P, _P],
+    "rbx_get_tables": [_J, _P, _P, _P, _P, _P, _P],
+    "rbx_direct_green": [_J, C.c_double, _P],
+    "rbx_forward": [_J, C.c_double, _P, _P],
+    "rbx_predict": [_J, C.c_double, _P],
+    "rbx_adjoint": [_J, C.c_double, _P, _P, C.c_int],
+    "rbx_update_from_tables": [_J, C.c_double, C.c_double, _P, C.POINTER(Stats)],
+    "rbx_update_frequency": [_J, C.c_double, C.c_double, _P, C.POINTER(Stats)],
+    "rbx_update_frequency_host": [_J, C.c_double, C.c_double, _P, _P, C.POINTER(Stats)],
+    "rbx_reconstruct": [_J, C.POINTER(C.c_double), C.c_int, _P, C.POINTER(Stats)],
+    "rbx_synchronize": [_J],
+    "rbx_destroy": [_J],
+}
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS) + ["rbx_last_error"]
+
+
+def load(path: str | None = None):
+    """Load librbx.so (built by paper_2211_00316_gb300.build); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB
+            if not os.path.exists(p):
+                raise RuntimeError(f"librbx.so not built ({p}); run __graft_entry__.build()")
+            L = C.CDLL(p)
+            for name, args in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            L.rbx_last_error.argtypes = [_J]
+            L.rbx_last_error.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return int(t)
+
+
+class Job:
+    """One reconstruction job: owns the library handle and its device workspaces."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        """Bind the job to `stream` (default: torch's current stream), so the library's
+        kernels are ordered with torch's copies into and out of the tensors passed here."""
+        self.L = load()
+        self.h = C.c_void_p()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        sp = self.stream.cuda_stream or None
+        self._check(self.L.rbx_create(C.byref(self.h), sp))
+        self.geom = None
+        self.N = self.X = self.nx = self.ny = 0
+
+    def _check(self, st: int):
+        if st != 0:
+            msg = self.L.rbx_last_error(self.h).decode() if getattr(self, "h", None) else ""
+            raise RbxError(st, msg)
+
+    def close(self):
+        if self.h:
+            self.L.rbx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- set-up
+    def set_geometry(self, g, precision: int = RBX_FP32, weight_mode: int | None = None, tau: float | None = None):
+        """g: a phantoms.Geometry (or any object with the same attributes)."""
+        G = Geometry(g.nx, g.ny, g.dx, g.x0, g.y0, g.n_xducers, g.ring_radius, g.mask_radius, g.c0, g.ds,
+                     g.weight_mode if weight_mode is None else weight_mode, g.tau if tau is None else tau, precision)
+        self._check(self.L.rbx_set_geometry(self.h, C.byref(G)))
+        self.geom = g
+        self.N, self.nx, self.ny = g.n_xducers, g.nx, g.ny
+        X = C.c_int()
+        self._check(self.L.rbx_mask(self.h, C.byref(X), None))
+        self.X = X.value
+
+    def mask_idx(self) -> torch.Tensor:
+        idx = torch.empty(self.X, dtype=torch.int32, device="cuda")
+        self._check(self.L.rbx_mask(self.h, None, _ptr(idx)))
+        self.sync()
+        return idx
+
+    def set_model(self, c: torch.Tensor):
+        self._check(self.L.rbx_set_model(self.h, _ptr(c)))
+
+    def get_model(self) -> torch.Tensor:
+        out = torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda")
+        self._check(self.L.rbx_get_model(self.h, _ptr(out)))
+        return out
+
+    # ---------------------------------------------------------------- steps
+    def trace_rays(self, f: float):
+        self._check(self.L.rbx_trace_rays(self.h, f))
+
+    def set_tables(self, T, a, gam, K, exits):
+        self._check(self.L.rbx_set_tables(self.h, _ptr(T), _ptr(a), _ptr(gam), _ptr(K), _ptr(exits)))
+
+    def get_tables(self):
+        N, X = self.N, self.X
+        T = torch.empty((N, X), dtype=torch.float32, device="cuda")
+        a, gam, dg = torch.empty_like(T), torch.empty_like(T), torch.empty_like(T)
+        K = torch.empty((N, X), dtype=torch.uint8, device="cuda")
+        ex = torch.empty((N, N - 1, 4), dtype=torch.float32, device="cuda")
+        self._check(self.L.rbx_get_tables(self.h, _ptr(T), _ptr(a), _ptr(gam), _ptr(K), _ptr(dg), _ptr(ex)))
+        self.sync()
+        return dict(T=T, a=a, gam=gam, K=K, dg=dg, exits=ex)
+
+    def direct_green(self, f: float) -> torch.Tensor:
+        out = torch.empty((self.N, self.N), dtype=torch.complex64, device="cuda")
+        self._check(self.L.rbx_direct_green(self.h, f, _ptr(out)))
+        return out
+
+    def forward(self, f: float, dm: torch.Tensor) -> torch.Tensor:
+        out = torch.empty((self.N, self.N), dtype=torch.complex64, device="cuda")
+        self._check(self.L.rbx_forward(self.h, f, _ptr(dm), _ptr(out)))
+        return out
+
+    def predict(self, f: float, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = out if out is not None else torch.empty((self.N, self.N), dtype=torch.complex64, device="cuda")
+        self._check(self.L.rbx_predict(self.h, f, _ptr(out)))
+        return out
+
+    def adjoint(self, f: float, R: torch.Tensor, preconditioned: bool) -> torch.Tensor:
+        out = torch.empty(self.X, dtype=torch.complex64, device="cuda")
+        self._check(self.L.rbx_adjoint(self.h, f, _ptr(R), _ptr(out), int(preconditioned)))
+        return out
+
+    def update_from_tables(self, f: float, df: float, data: torch.Tensor) -> dict:
+        st = Stats()
+        self._check(self.L.rbx_update_from_tables(self.h, f, df, _ptr(data), C.byref(st)))
+        return st.as_dict()
+
+    def update_frequency(self, f: float, df: float, data: torch.Tensor) -> dict:
+        st = Stats()
+        self._check(self.L.rbx_update_frequency(self.h, f, df, _ptr(data), C.byref(st)))
+        return st.as_dict()
+
+    def update_frequency_host(self, f: float, df: float, data_host, c_out_host=None) -> dict:
+        st = Stats()
+        self._check(self.L.rbx_update_frequency_host(self.h, f, df, _ptr(data_host), _ptr(c_out_host),
+                                                     C.byref(st)))
+        return st.as_dict()
+
+    def reconstruct(self, freqs, data: torch.Tensor) -> list[dict]:
+        fr = np.ascontiguousarray(freqs, dtype=np.float64)
+        sts = (Stats * len(fr))()
+        self._check(self.L.rbx_reconstruct(self.h, fr.ctypes.data_as(C.POINTER(C.c_double)), len(fr), _ptr(data),
+                                           sts))
+        return [s.as_dict() for s in sts]
+
+    def sync(self):
+        self._check(self.L.rbx_synchronize(self.h))
