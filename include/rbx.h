@@ -173,6 +173,23 @@ rbx_status rbx_update_frequency_host(rbx_job *job, double freq_hz, double dfreq_
  * nf == 1). per_freq (host, nf entries) may be NULL. */
 rbx_status rbx_reconstruct(rbx_job *job, const double *freqs_hz, int nf, const void *data_dev, rbx_stats *per_freq);
 
+/* Born forward for callers that cannot allocate device memory (inside a CUDA-graph capture
+ * that must not add allocation nodes, under a framework allocator that owns the device, or
+ * in services that forbid allocation after start-up). The paper has no counterpart: this is
+ * a deployment variant of rbx_forward that needs no job. It computes
+ * D[e*N + r] = sum_x G_r[x] G_e[x] v[x] from caller tables T_dev, a_dev (float32) and K_dev
+ * (uint8), each [n_xducers][n_nodes] as in rbx_set_tables (a = 0: uncovered), and the Born
+ * weights v_dev (n_nodes float32, v = omega^2 dA dm per mask node); D_dev is N x N complex64.
+ * It allocates nothing: the split partial sums live in a fixed 8 MiB array inside the
+ * library, so n_xducers must be <= 1024 (RBX_EINVAL otherwise). The first call on each
+ * device looks up that array's device address (it may load the module): make it before any
+ * stream capture. All calls share the array; calls that overlap on the GPU race and must be
+ * serialised by the caller. Work is queued on cuda_stream (NULL: legacy default stream).
+ * err (errlen bytes, may be NULL) receives a message, "" on success. */
+rbx_status rbx_forward_noalloc(const float *T_dev, const float *a_dev, const uint8_t *K_dev, const float *v_dev,
+                               int n_xducers, int n_nodes, double freq_hz, double c0, void *D_dev, void *cuda_stream,
+                               char *err, size_t errlen);
+
 /* Last error message of the job ("" if none). The string lives as long as the job. */
 const char *rbx_last_error(const rbx_job *job);
 

@@ -71,6 +71,8 @@ _SIGS = {
     "rbx_reconstruct": [_J, C.POINTER(C.c_double), C.c_int, _P, C.POINTER(Stats)],
     "rbx_synchronize": [_J],
     "rbx_destroy": [_J],
+    "rbx_forward_noalloc": [_P, _P, _P, _P, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, C.c_char_p,
+                            C.c_size_t],
 }
 
 
