@@ -1,0 +1,516 @@
+// Steps a6-a8 on the 5th-generation tensor cores (tcgen05, BF16 inputs, FP32 accumulation
+// in tensor memory), for the BF16 precision of the library.
+//
+// Complex operands are kept as planar BF16 (re and im planes, K-major). One complex
+// multiply-accumulate is four real MMAs into two accumulators; the -Im*Im term uses the
+// instruction descriptor's negate-A bit, so no negated copy is stored:
+//   acc_re += A_re B_re^T - A_im B_im^T,   acc_im += A_re B_im^T + A_im B_re^T.
+//
+// Forward (Eqs. perturb1, derivative): D = G diag(v) G^T, M = e (128), N = r (128),
+// K = mask nodes, upper tile pairs only, K split over CTAs, FP32 partials reduced in a
+// fixed order (shared with the FP32 path).
+// Back-projection (Eq. sound_speed_update2, factorised): for a tile of 128 mask nodes and
+// 128 emitters, P0 = U^T R_s and P1 = (conj(kappa) U)^T R_s share the R_s tiles (8 MMAs
+// per K step, 4 accumulators = all 512 TMEM columns); the epilogue forms
+// sum_e [u_e P0 + s kappa_e u_e P1] per node from tensor memory and the bf16 planes.
+//
+// Warp roles (192 threads, one CTA per SM): warp 0 issues TMA loads, warp 1 owns tensor
+// memory and issues the MMAs from one thread, warps 2-5 drain the accumulators (warp w
+// reads TMEM lanes 32 (w mod 4) .. +31).
+#include "rbx_internal.cuh"
+#include "tc_sm100.cuh"
+
+#include <cuda_bf16.h>
+#include <mutex>
+
+namespace rbx {
+using namespace tc;
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr uint32_t TILE = BM * BK * 2;        // 16 KB: 128 rows x 64 BF16 (128 B per row)
+
+constexpr int F_STAGES = 3, F_TILES = 4;     // forward: Gre, Gim | Gvre, Gvim
+constexpr size_t F_SMEM = 1024 + (size_t)F_STAGES * F_TILES * TILE + 256;
+constexpr int B_STAGES = 2, B_TILES = 6;     // back-projection: Ure, Uim, Vre, Vim | Rsre, Rsim
+constexpr size_t B_SMEM = 1024 + (size_t)B_STAGES * B_TILES * TILE + 256;
+
+__device__ __forceinline__ float phase_cycles_tc(float T, int K, float fhi, float flo)
+{
+    float p = fhi * T;
+    float err = fmaf(fhi, T, -p) + flo * T;
+    float r = (p - rintf(p)) + err;
+    return r + 0.125f - 0.25f * (float)K;
+}
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p)
+{
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+}
+
+// ---------------------------------------------------------------- forward
+
+__global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ CUtensorMap mGre,
+                                                       const __grid_constant__ CUtensorMap mGim,
+                                                       const __grid_constant__ CUtensorMap mGvre,
+                                                       const __grid_constant__ CUtensorMap mGvim, int N, int ntile,
+                                                       int nk, int kper, float2 *__restrict__ part,
+                                                       unsigned *__restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = align1024(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)F_STAGES * F_TILES * TILE);
+    uint64_t *empty = full + F_STAGES;
+    uint64_t *accb = empty + F_STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    int b = blockIdx.x, te = 0;
+    while (b >= ntile - te) { b -= ntile - te; te++; }
+    const int tr = te + b;
+    const int split = blockIdx.y;
+    const int c0 = split * kper, nc = min(nk, c0 + kper) - c0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < F_STAGES; s++) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        mbar_init(accb, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, 256);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&mGre); prefetch_tmap(&mGim); prefetch_tmap(&mGvre); prefetch_tmap(&mGvim);
+        int issued = 0;
+        for (int c = 0; c < nc; c++) {
+            int s = c % F_STAGES;
+            if (c >= F_STAGES && !mbar_wait(empty + s, ((c / F_STAGES) - 1) & 1)) { atomicOr(err, 1u); break; }
+            mbar_arrive_expect_tx(full + s, F_TILES * TILE);
+            uint32_t base = smem_u32(tiles + (size_t)s * F_TILES * TILE);
+            int kx = (c0 + c) * BK;
+            tma_load_2d(base, &mGre, full + s, kx, te * BM);
+            tma_load_2d(base + TILE, &mGim, full + s, kx, te * BM);
+            tma_load_2d(base + 2 * TILE, &mGvre, full + s, kx, tr * BN);
+            tma_load_2d(base + 3 * TILE, &mGvim, full + s, kx, tr * BN);
+            issued++;
+        }
+        // no copy may still be in flight when the CTA retires
+        for (int c = (issued > F_STAGES ? issued - F_STAGES : 0); c < issued; c++)
+            if (!mbar_wait(full + (c % F_STAGES), (c / F_STAGES) & 1)) atomicOr(err, 4u);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t ip = idesc_bf16(BM, BN, 0), in = idesc_bf16(BM, BN, 1);
+            const uint32_t dre = tmem, dim = tmem + BN;
+            for (int c = 0; c < nc; c++) {
+                int s = c % F_STAGES;
+                if (!mbar_wait(full + s, (c / F_STAGES) & 1)) { atomicOr(err, 2u); break; }
+                fence_after();
+                uint32_t base = smem_u32(tiles + (size_t)s * F_TILES * TILE);
+#pragma unroll
+                for (int k = 0; k < BK / 16; k++) {
+                    uint64_t a0 = desc_sw128(base + k * 32), a1 = desc_sw128(base + TILE + k * 32);
+                    uint64_t b0 = desc_sw128(base + 2 * TILE + k * 32), b1 = desc_sw128(base + 3 * TILE + k * 32);
+                    uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                    mma_bf16(dre, a0, b0, ip, acc);
+                    mma_bf16(dre, a1, b1, in, 1u);
+                    mma_bf16(dim, a0, b1, ip, acc);
+                    mma_bf16(dim, a1, b0, ip, 1u);
+                }
+                mma_commit(empty + s);
+            }
+            mma_commit(accb);
+            if (!mbar_wait(accb, 0)) atomicOr(err, 8u);
+        }
+        __syncwarp();
+    } else if (warp >= 2) {
+        const int sub = warp & 3, row = sub * 32 + lane;
+        bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0));
+        fence_after();
+        if (ok) {
+            const int e = te * BM + row;
+            float2 *P = part + (size_t)split * N * N + (size_t)e * N;
+            const uint32_t lanes = (uint32_t)(sub * 32) << 16;
+#pragma unroll 1
+            for (int cc = 0; cc < BN; cc += 32) {
+                float vr[32], vi[32];
+                tmem_ld32(tmem + lanes + cc, vr);
+                tmem_ld32(tmem + lanes + BN + cc, vi);
+                if (e < N) {
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        int r = tr * BN + cc + i;
+                        if (r < N) P[r] = make_float2(vr[i], vi[i]);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicOr(err, 16u);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// ---------------------------------------------------------------- back-projection
+
+__global__ __launch_bounds__(192, 1) void k_backproject_tc(
+    const __grid_constant__ CUtensorMap mUre, const __grid_constant__ CUtensorMap mUim,
+    const __grid_constant__ CUtensorMap mVre, const __grid_constant__ CUtensorMap mVim,
+    const __grid_constant__ CUtensorMap mRre, const __grid_constant__ CUtensorMap mRim,
+    const __nv_bfloat16 *__restrict__ planes, size_t pstride, int Npad, int nk, float sgn, float2 *__restrict__ bpart,
+    int Xp, unsigned *__restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = align1024(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)B_STAGES * B_TILES * TILE);
+    uint64_t *empty = full + B_STAGES;
+    uint64_t *accb = empty + B_STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int et = blockIdx.x, xt = blockIdx.y;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < B_STAGES; s++) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+        mbar_init(accb, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&mUre); prefetch_tmap(&mUim); prefetch_tmap(&mVre); prefetch_tmap(&mVim);
+        prefetch_tmap(&mRre); prefetch_tmap(&mRim);
+        int issued = 0;
+        for (int c = 0; c < nk; c++) {
+            int s = c % B_STAGES;
+            if (c >= B_STAGES && !mbar_wait(empty + s, ((c / B_STAGES) - 1) & 1)) { atomicOr(err, 1u); break; }
+            mbar_arrive_expect_tx(full + s, B_TILES * TILE);
+            uint32_t base = smem_u32(tiles + (size_t)s * B_TILES * TILE);
+            int kx = c * BK;
+            tma_load_2d(base, &mUre, full + s, kx, xt * BM);
+            tma_load_2d(base + TILE, &mUim, full + s, kx, xt * BM);
+            tma_load_2d(base + 2 * TILE, &mVre, full + s, kx, xt * BM);
+            tma_load_2d(base + 3 * TILE, &mVim, full + s, kx, xt * BM);
+            tma_load_2d(base + 4 * TILE, &mRre, full + s, kx, et * BN);
+            tma_load_2d(base + 5 * TILE, &mRim, full + s, kx, et * BN);
+            issued++;
+        }
+        for (int c = (issued > B_STAGES ? issued - B_STAGES : 0); c < issued; c++)
+            if (!mbar_wait(full + (c % B_STAGES), (c / B_STAGES) & 1)) atomicOr(err, 4u);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t ip = idesc_bf16(BM, BN, 0), in = idesc_bf16(BM, BN, 1);
+            const uint32_t p0r = tmem, p0i = tmem + BN, p1r = tmem + 2 * BN, p1i = tmem + 3 * BN;
+            for (int c = 0; c < nk; c++) {
+                int s = c % B_STAGES;
+                if (!mbar_wait(full + s, (c / B_STAGES) & 1)) { atomicOr(err, 2u); break; }
+                fence_after();
+                uint32_t base = smem_u32(tiles + (size_t)s * B_TILES * TILE);
+#pragma unroll
+                for (int k = 0; k < BK / 16; k++) {
+                    uint64_t ur = desc_sw128(base + k * 32), ui = desc_sw128(base + TILE + k * 32);
+                    uint64_t vr = desc_sw128(base + 2 * TILE + k * 32), vi = desc_sw128(base + 3 * TILE + k * 32);
+                    uint64_t rr = desc_sw128(base + 4 * TILE + k * 32), ri = desc_sw128(base + 5 * TILE + k * 32);
+                    uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                    mma_bf16(p0r, ur, rr, ip, acc);
+                    mma_bf16(p0r, ui, ri, in, 1u);
+                    mma_bf16(p0i, ur, ri, ip, acc);
+                    mma_bf16(p0i, ui, rr, ip, 1u);
+                    mma_bf16(p1r, vr, rr, ip, acc);
+                    mma_bf16(p1r, vi, ri, in, 1u);
+                    mma_bf16(p1i, vr, ri, ip, acc);
+                    mma_bf16(p1i, vi, rr, ip, 1u);
+                }
+                mma_commit(empty + s);
+            }
+            mma_commit(accb);
+            if (!mbar_wait(accb, 0)) atomicOr(err, 8u);
+        }
+        __syncwarp();
+    } else if (warp >= 2) {
+        const int sub = warp & 3, row = sub * 32 + lane;
+        bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0));
+        fence_after();
+        const int x = xt * BM + row;
+        float gre = 0.f, gim = 0.f;
+        if (ok) {
+            const uint32_t lanes = (uint32_t)(sub * 32) << 16;
+            // epilogue weights at [x][e]: u (planes 0, 1) and kappa u (planes 4, 5)
+            const __nv_bfloat16 *w0r = planes + (size_t)x * Npad + et * BN;
+            const __nv_bfloat16 *w0i = w0r + pstride, *w1r = w0r + 4 * pstride, *w1i = w0r + 5 * pstride;
+#pragma unroll 1
+            for (int cc = 0; cc < BN; cc += 32) {
+                float a0r[32], a0i[32], a1r[32], a1i[32];
+                tmem_ld32(tmem + lanes + cc, a0r);
+                tmem_ld32(tmem + lanes + BN + cc, a0i);
+                tmem_ld32(tmem + lanes + 2 * BN + cc, a1r);
+                tmem_ld32(tmem + lanes + 3 * BN + cc, a1i);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    uint4 r0 = *reinterpret_cast<const uint4 *>(w0r + cc + 8 * q);
+                    uint4 i0 = *reinterpret_cast<const uint4 *>(w0i + cc + 8 * q);
+                    uint4 r1 = *reinterpret_cast<const uint4 *>(w1r + cc + 8 * q);
+                    uint4 i1 = *reinterpret_cast<const uint4 *>(w1i + cc + 8 * q);
+                    const __nv_bfloat162 *R0 = reinterpret_cast<const __nv_bfloat162 *>(&r0);
+                    const __nv_bfloat162 *I0 = reinterpret_cast<const __nv_bfloat162 *>(&i0);
+                    const __nv_bfloat162 *R1 = reinterpret_cast<const __nv_bfloat162 *>(&r1);
+                    const __nv_bfloat162 *I1 = reinterpret_cast<const __nv_bfloat162 *>(&i1);
+#pragma unroll
+                    for (int h = 0; h < 4; h++) {
+                        float2 wr0 = __bfloat1622float2(R0[h]), wi0 = __bfloat1622float2(I0[h]);
+                        float2 wr1 = __bfloat1622float2(R1[h]), wi1 = __bfloat1622float2(I1[h]);
+                        int j = 8 * q + 2 * h;
+                        gre += wr0.x * a0r[j] - wi0.x * a0i[j] + sgn * (wr1.x * a1r[j] - wi1.x * a1i[j]);
+                        gim += wr0.x * a0i[j] + wi0.x * a0r[j] + sgn * (wr1.x * a1i[j] + wi1.x * a1r[j]);
+                        gre += wr0.y * a0r[j + 1] - wi0.y * a0i[j + 1] + sgn * (wr1.y * a1r[j + 1] - wi1.y * a1i[j + 1]);
+                        gim += wr0.y * a0i[j + 1] + wi0.y * a0r[j + 1] + sgn * (wr1.y * a1i[j + 1] + wi1.y * a1r[j + 1]);
+                    }
+                }
+            }
+            bpart[(size_t)et * Xp + x] = make_float2(gre, gim);
+        } else if (lane == 0) {
+            atomicOr(err, 16u);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------- operand synthesis
+
+// planes [4][Npad][Xpad]: Gre, Gim, (G v)re, (G v)im ; G_e[x] = C a exp(i 2 pi (f T - K/4 + 1/8))
+__global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float *__restrict__ v, int N, int X, int Xpad,
+                               size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)N * X) return;
+    int e = (int)(i / X), x = (int)(i % X);
+    TabEntry t = tab[i];
+    float gr = 0.f, gi = 0.f;
+    if (t.idk != kUncovered) {
+        float s, c;
+        sincospif(2.f * phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &s, &c);
+        gr = C * t.a * c;
+        gi = C * t.a * s;
+    }
+    float vv = v[x];
+    size_t o = (size_t)e * Xpad + x;
+    planes[o] = __float2bfloat16_rn(gr);
+    planes[pstride + o] = __float2bfloat16_rn(gi);
+    planes[2 * pstride + o] = __float2bfloat16_rn(gr * vv);
+    planes[3 * pstride + o] = __float2bfloat16_rn(gi * vv);
+}
+
+// planes [6][Xp][Npad] at [x][e]: u, conj(kappa) u, kappa u (re, im each);
+// u_e[x] = dgamma / (C a) exp(-i 2 pi (f T - K/4 + 1/8)), kappa = exp(i gamma)
+__global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, const float *__restrict__ dg, int N, int X, int Npad,
+                              size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes)
+{
+    __shared__ float sv[6][32][33];
+    const int x0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int q = ty; q < 32; q += 8) {
+        int e = e0 + q, x = x0 + tx;
+        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (e < N && x < X) {
+            size_t i = (size_t)e * X + x;
+            TabEntry t = tab[i];
+            if (t.idk != kUncovered) {
+                float s, c, sg, cg;
+                sincospif(2.f * phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &s, &c);
+                sincosf(t.gam, &sg, &cg);
+                float A = dg[i] / (C * t.a);
+                float ur = A * c, ui = -A * s;
+                v[0] = ur; v[1] = ui;
+                v[2] = cg * ur + sg * ui; v[3] = cg * ui - sg * ur;   // conj(kappa) u
+                v[4] = cg * ur - sg * ui; v[5] = cg * ui + sg * ur;   // kappa u
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) sv[k][q][tx] = v[k];
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+        int x = x0 + q, e = e0 + tx;
+        if (x < X && e < N) {
+            size_t o = (size_t)x * Npad + e;
+#pragma unroll
+            for (int k = 0; k < 6; k++) planes[k * pstride + o] = __float2bfloat16_rn(sv[k][tx][q]);
+        }
+    }
+}
+
+// R_s (complex N x N) -> planes [2][Npad][Npad]
+__global__ void k_rs_planes(const float2 *__restrict__ Rs, int N, int Npad, __nv_bfloat16 *__restrict__ planes)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)N * N) return;
+    int e = (int)(i / N), r = (int)(i % N);
+    float2 v = Rs[i];
+    size_t o = (size_t)e * Npad + r;
+    planes[o] = __float2bfloat16_rn(v.x);
+    planes[(size_t)Npad * Npad + o] = __float2bfloat16_rn(v.y);
+}
+
+// gpart[0][x] = sum over emitter tiles (fixed order); gpart[1][x] = 0 (the stacks are
+// already combined with their sign in the epilogue)
+__global__ void k_bp_reduce(const float2 *__restrict__ bpart, int ET, int Xp, int X, float2 *__restrict__ gpart)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= X) return;
+    float2 s = make_float2(0.f, 0.f);
+    for (int t = 0; t < ET; t++) {
+        float2 p = bpart[(size_t)t * Xp + x];
+        s.x += p.x;
+        s.y += p.y;
+    }
+    gpart[x] = s;
+    gpart[(size_t)X + x] = make_float2(0.f, 0.f);
+}
+
+// ---------------------------------------------------------------- host helpers
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// BF16 matrix [rows][cols] (cols contiguous, K-major) read in 128-row x 64-column boxes
+bool make_map(CUtensorMap *m, const void *base, size_t rows, size_t cols)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- API used by rbx_api.cu
+
+bool tc_setup(TcPlanes &p, int N, int X)
+{
+    p.N = N;
+    p.X = X;
+    p.Npad = (N + BM - 1) / BM * BM;
+    p.Xpad = (X + BK - 1) / BK * BK;
+    p.Xp = (X + BM - 1) / BM * BM;
+    p.fwd_pstride = (size_t)p.Npad * p.Xpad;
+    p.bp_pstride = (size_t)p.Xp * p.Npad;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    p.sms = sms;
+    int T = p.Npad / BM, pairs = T * (T + 1) / 2;
+    int nk = p.Xpad / BK;
+    int splits = pairs >= sms ? 1 : sms / pairs;
+    if (splits > nk) splits = nk;
+    int kper = (nk + splits - 1) / splits;
+    p.fwd_kper = kper;
+    p.fwd_splits = (nk + kper - 1) / kper;
+    if (cudaMalloc(&p.fplanes, 4 * p.fwd_pstride * sizeof(__nv_bfloat16)) != cudaSuccess) return false;
+    if (cudaMalloc(&p.bplanes, 6 * p.bp_pstride * sizeof(__nv_bfloat16)) != cudaSuccess) return false;
+    if (cudaMalloc(&p.rsplanes, 2 * (size_t)p.Npad * p.Npad * sizeof(__nv_bfloat16)) != cudaSuccess) return false;
+    if (cudaMalloc(&p.bpart, (size_t)(p.Npad / BN) * p.Xp * sizeof(float2)) != cudaSuccess) return false;
+    if (cudaMalloc(&p.err, sizeof(unsigned)) != cudaSuccess) return false;
+    cudaMemset(p.fplanes, 0, 4 * p.fwd_pstride * sizeof(__nv_bfloat16));
+    cudaMemset(p.bplanes, 0, 6 * p.bp_pstride * sizeof(__nv_bfloat16));
+    cudaMemset(p.rsplanes, 0, 2 * (size_t)p.Npad * p.Npad * sizeof(__nv_bfloat16));
+    cudaMemset(p.err, 0, sizeof(unsigned));
+    const __nv_bfloat16 *f = static_cast<const __nv_bfloat16 *>(p.fplanes);
+    const __nv_bfloat16 *b = static_cast<const __nv_bfloat16 *>(p.bplanes);
+    const __nv_bfloat16 *r = static_cast<const __nv_bfloat16 *>(p.rsplanes);
+    bool ok = true;
+    for (int k = 0; k < 4; k++) ok = ok && make_map(&p.fmaps[k], f + k * p.fwd_pstride, p.Npad, p.Xpad);
+    for (int k = 0; k < 4; k++) ok = ok && make_map(&p.bmaps[k], b + k * p.bp_pstride, p.Xp, p.Npad);
+    for (int k = 0; k < 2; k++) ok = ok && make_map(&p.bmaps[4 + k], r + (size_t)k * p.Npad * p.Npad, p.Npad, p.Npad);
+    if (!ok) return false;
+    ok = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(k_backproject_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM) ==
+             cudaSuccess;
+    p.ready = ok;
+    return ok;
+}
+
+void tc_free(TcPlanes &p)
+{
+    void *ps[] = {p.fplanes, p.bplanes, p.rsplanes, p.bpart, p.err};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    p = TcPlanes{};
+}
+
+static float green_const_tc(double f, double c0)
+{
+    return (float)(1.0 / sqrt(8.0 * 3.14159265358979323846 * (2.0 * 3.14159265358979323846 * f) / c0));
+}
+
+int launch_forward_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, float2 *part,
+                      cudaStream_t s)
+{
+    size_t n = (size_t)p.N * p.X;
+    float fhi = (float)f, flo = (float)(f - (double)fhi);
+    k_synth_fwd_tc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, v, p.N, p.X, p.Xpad, p.fwd_pstride, fhi, flo,
+                                                               green_const_tc(f, c0),
+                                                               static_cast<__nv_bfloat16 *>(p.fplanes));
+    int T = p.Npad / BM, pairs = T * (T + 1) / 2;
+    k_forward_tc<<<dim3(pairs, p.fwd_splits), 192, F_SMEM, s>>>(p.fmaps[0], p.fmaps[1], p.fmaps[2], p.fmaps[3], p.N, T,
+                                                                p.Xpad / BK, p.fwd_kper, part, p.err);
+    return p.fwd_splits;
+}
+
+void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, double f, double c0, cudaStream_t s)
+{
+    float fhi = (float)f, flo = (float)(f - (double)fhi);
+    dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
+    k_synth_bp_tc<<<grd, 256, 0, s>>>(tab, dg, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
+                                      static_cast<__nv_bfloat16 *>(p.bplanes));
+}
+
+void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s)
+{
+    size_t nn = (size_t)p.N * p.N;
+    k_rs_planes<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Rs, p.N, p.Npad,
+                                                             static_cast<__nv_bfloat16 *>(p.rsplanes));
+    dim3 grd(p.Npad / BN, p.Xp / BM);
+    k_backproject_tc<<<grd, 192, B_SMEM, s>>>(p.bmaps[0], p.bmaps[1], p.bmaps[2], p.bmaps[3], p.bmaps[4], p.bmaps[5],
+                                              static_cast<const __nv_bfloat16 *>(p.bplanes), p.bp_pstride, p.Npad,
+                                              p.Npad / BK, weight_mode == 0 ? -1.f : 1.f, p.bpart, p.Xp, p.err);
+    k_bp_reduce<<<(p.X + 255) / 256, 256, 0, s>>>(p.bpart, p.Npad / BN, p.Xp, p.X, gpart);
+}
+
+}  // namespace rbx

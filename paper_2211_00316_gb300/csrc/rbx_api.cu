@@ -69,6 +69,7 @@ static void free_ws(Workspace &w)
                   w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters};
     for (void *p : ps)
         if (p) cudaFree(p);
+    tc_free(w.tc);
     w = Workspace{};
 }
 
@@ -151,7 +152,8 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     NEED(j, std::isfinite(g.ds) && g.ds > 0, RBX_EINVAL, "ds must be > 0");
     NEED(j, g.weight_mode == 0 || g.weight_mode == 1, RBX_EINVAL, "weight_mode must be 0 or 1");
     NEED(j, std::isfinite(g.tau), RBX_EINVAL, "tau must be finite");
-    NEED(j, g.precision >= 0 && g.precision <= 2, RBX_EINVAL, "precision must be 0, 1 or 2");
+    NEED(j, g.precision == RBX_FP32 || g.precision == RBX_BF16, RBX_EINVAL,
+         "precision must be RBX_FP32 or RBX_BF16 (split BF16 is not available yet)");
     double xl = g.x0, xr = g.x0 + (g.nx - 1) * g.dx, yl = g.y0, yr = g.y0 + (g.ny - 1) * g.dx;
     NEED(j, xl <= -g.ring_radius - g.dx && xr >= g.ring_radius + g.dx && yl <= -g.ring_radius - g.dx &&
                 yr >= g.ring_radius + g.dx,
@@ -204,6 +206,14 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     ALLOC(w.R, N * N);
     ALLOC(w.Rs, N * N);
     ALLOC(w.data, N * N);
+    if (g.precision != RBX_FP32) {
+        if (!tc_setup(w.tc, w.N, X)) {
+            cudaGetLastError();
+            free_ws(w);
+            return fail(j, RBX_ENOMEM, "tensor-core operand set-up failed (allocation or TMA descriptor)");
+        }
+        if (w.tc.fwd_splits > w.fwd_splits) w.fwd_splits = w.tc.fwd_splits;
+    }
     ALLOC(w.part, (size_t)w.fwd_splits * N * N);
     ALLOC(w.gpart, 2 * (size_t)X);
     size_t nred = (size_t)residual_blocks(w.N) + 8;
@@ -347,12 +357,20 @@ static rbx_status forward_core(rbx_job *j, double f, bool timed)
 {
     Workspace &w = j->w;
     rbx_status st;
-    launch_synth_fwd(w.tab, w.N, w.X, f, j->g.c0, w.G, j->stream);
-    LAUNCHED(j, 1);
-    if (timed && (st = record(j, EV_SYNTH_F))) return st;
-    launch_forward_simt(w.G, w.v, w.N, w.X, w.fwd_splits, w.part, j->stream);
-    launch_forward_reduce(w.part, w.N, w.fwd_splits, w.D, j->stream);
-    LAUNCHED(j, 2);
+    if (j->g.precision == RBX_BF16) {
+        // the BF16 operand synthesis is fused into the first launch of launch_forward_tc
+        if (timed && (st = record(j, EV_SYNTH_F))) return st;
+        int splits = launch_forward_tc(w.tc, w.tab, w.v, f, j->g.c0, w.part, j->stream);
+        launch_forward_reduce(w.part, w.N, splits, w.D, j->stream);
+        LAUNCHED(j, 3);
+    } else {
+        launch_synth_fwd(w.tab, w.N, w.X, f, j->g.c0, w.G, j->stream);
+        LAUNCHED(j, 1);
+        if (timed && (st = record(j, EV_SYNTH_F))) return st;
+        launch_forward_simt(w.G, w.v, w.N, w.X, w.fwd_splits, w.part, j->stream);
+        launch_forward_reduce(w.part, w.N, w.fwd_splits, w.D, j->stream);
+        LAUNCHED(j, 2);
+    }
     if (timed && (st = record(j, EV_GEMM_F))) return st;
     return RBX_OK;
 }
@@ -396,7 +414,12 @@ rbx_status rbx_adjoint(rbx_job *j, double f, const void *R_dev, void *out_dev, i
     Workspace &w = j->w;
     launch_symmetrize(static_cast<const float2 *>(R_dev), w.N, w.Rs, j->stream);
     LAUNCHED(j, 1);
-    if (preconditioned) {
+    if (preconditioned && j->g.precision == RBX_BF16) {
+        launch_synth_bp_tc(w.tc, w.tab, w.dg, f, j->g.c0, j->stream);
+        launch_backproject_tc(w.tc, w.Rs, j->g.weight_mode, w.gpart, j->stream);
+        launch_combine_adjoint(w.gpart, w.X, 0, j->g.weight_mode, 2.0, static_cast<float2 *>(out_dev), j->stream);
+        LAUNCHED(j, 1);
+    } else if (preconditioned) {
         launch_synth_bp(w.tab, w.dg, w.N, w.X, f, j->g.c0, w.U, w.kap, j->stream);
         launch_backproject_simt(w.U, w.kap, w.Rs, w.N, w.X, 0, w.gpart, j->stream);
         launch_combine_adjoint(w.gpart, w.X, 0, j->g.weight_mode, 2.0, static_cast<float2 *>(out_dev), j->stream);
@@ -429,11 +452,19 @@ static rbx_status update_core(rbx_job *j, double f, double df, const float2 *dat
     double r2 = 0;
     CUDA_TRY(j, cudaMemcpyAsync(&r2, w.red + residual_blocks(w.N), sizeof r2, cudaMemcpyDeviceToHost, j->stream));
     if ((st = record(j, EV_RESID))) return st;
-    launch_synth_bp(w.tab, w.dg, w.N, w.X, f, j->g.c0, w.U, w.kap, j->stream);
-    LAUNCHED(j, 1);
-    if ((st = record(j, EV_SYNTH_B))) return st;
-    launch_backproject_simt(w.U, w.kap, w.Rs, w.N, w.X, 0, w.gpart, j->stream);
-    LAUNCHED(j, 1);
+    if (j->g.precision == RBX_BF16) {
+        launch_synth_bp_tc(w.tc, w.tab, w.dg, f, j->g.c0, j->stream);
+        LAUNCHED(j, 1);
+        if ((st = record(j, EV_SYNTH_B))) return st;
+        launch_backproject_tc(w.tc, w.Rs, j->g.weight_mode, w.gpart, j->stream);
+        LAUNCHED(j, 3);
+    } else {
+        launch_synth_bp(w.tab, w.dg, w.N, w.X, f, j->g.c0, w.U, w.kap, j->stream);
+        LAUNCHED(j, 1);
+        if ((st = record(j, EV_SYNTH_B))) return st;
+        launch_backproject_simt(w.U, w.kap, w.Rs, w.N, w.X, 0, w.gpart, j->stream);
+        LAUNCHED(j, 1);
+    }
     if ((st = record(j, EV_GEMM_B))) return st;
     launch_update(w.gpart, w.node2x, w.nx, w.ny, w.X, j->g.weight_mode, f, df, j->g.tau, j->g.c0, w.c, w.red,
                   w.counters, j->stream);
@@ -470,6 +501,11 @@ static rbx_status update_core(rbx_job *j, double f, double df, const float2 *dat
         out->ms_kernel[RBX_K_SYNTH_BP] = elapsed(j, EV_RESID, EV_SYNTH_B);
         out->ms_kernel[RBX_K_GEMM_BP] = elapsed(j, EV_SYNTH_B, EV_GEMM_B);
         out->ms_kernel[RBX_K_UPDATE] = elapsed(j, EV_GEMM_F, EV_RESID) + elapsed(j, EV_GEMM_B, EV_UPDATE);
+    }
+    if (w.tc.err) {
+        unsigned terr = 0;
+        CUDA_TRY(j, cudaMemcpy(&terr, w.tc.err, sizeof terr, cudaMemcpyDeviceToHost));
+        NEED(j, terr == 0, RBX_ETIMEOUT, "a tensor-core kernel's bounded wait gave up");
     }
     NEED(j, cnt[4] == 0, RBX_ENUMERIC, "non-finite or non-positive updated squared slowness");
     NEED(j, cnt[2] == 0, RBX_ENUMERIC, "a ray did not reach the ring within the step limit");

@@ -1,5 +1,6 @@
 // Internal declarations of the rbx CUDA library (not part of the public ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -28,6 +29,21 @@ struct RayParams {
     int maxs;
 };
 
+// BF16 tensor-core operands of one job: planar complex planes, their TMA descriptors and
+// the back-projection partials (k_gemm_tc.cu).
+struct TcPlanes {
+    int N = 0, X = 0, Npad = 0, Xpad = 0, Xp = 0, sms = 0;
+    size_t fwd_pstride = 0, bp_pstride = 0;
+    int fwd_splits = 1, fwd_kper = 1;
+    void *fplanes = nullptr;   // [4][Npad][Xpad] bf16: Gre, Gim, (Gv)re, (Gv)im
+    void *bplanes = nullptr;   // [6][Xp][Npad] bf16: u, conj(kappa) u, kappa u (re, im)
+    void *rsplanes = nullptr;  // [2][Npad][Npad] bf16: R_s re, im
+    float2 *bpart = nullptr;   // [Npad/128][Xp] partial back-projection
+    unsigned *err = nullptr;   // bounded-wait timeouts of the tensor-core kernels
+    CUtensorMap fmaps[4], bmaps[6];
+    bool ready = false;
+};
+
 // Device workspace of one job.
 struct Workspace {
     int N = 0, X = 0, nx = 0, ny = 0;
@@ -44,6 +60,7 @@ struct Workspace {
     double *red = nullptr;           // reduction scratch
     unsigned long long *counters = nullptr;   // [0] uncovered [1] clamped [2] bad rays [3] CAS bound [4] m <= 0 [5] bad model [6] mask count
     int fwd_splits = 1;
+    TcPlanes tc;
 };
 
 // ---------------------------------------------------------------- kernels (launchers)
@@ -78,6 +95,14 @@ void launch_forward_reduce(const float2 *part, int N, int splits, float2 *D, cud
 // mode 0: preconditioned (A = U, conj(kap) U; W = U, kap U); mode 1: plain adjoint (A = W = conj(G))
 void launch_backproject_simt(const float2 *A, const float2 *kap, const float2 *Rs, int N, int X, int mode,
                              float2 *gpart, cudaStream_t s);
+
+// k_gemm_tc.cu (BF16 tensor cores)
+bool tc_setup(TcPlanes &p, int N, int X);
+void tc_free(TcPlanes &p);
+int launch_forward_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, float2 *part,
+                      cudaStream_t s);
+void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, double f, double c0, cudaStream_t s);
+void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s);
 
 // k_update.cu
 void launch_residual(const float2 *gdir, const float2 *D, const float2 *data, int N, float2 *R, float2 *Rs,

@@ -1,0 +1,114 @@
+"""BF16 tensor-core path (tcgen05) against the FP64 oracle.
+
+Tolerance (the benchmark spec): forward / back-projection relative L2 <= 5e-3 on identical
+(oracle, FP32-rounded) tables; one update <= 0.05 m/s RMS from the oracle's."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2211_00316_gb300 import phantoms as P
+from paper_2211_00316_gb300 import rbx
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def dev(x, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+class Case:
+    def __init__(self, oracle_mod, w, f, weight_mode=0):
+        self.w, self.g, self.f = w, w.geom, f
+        self.o = oracle_mod.Oracle(self.g, weight_mode=weight_mode)
+        self.c32 = w.c_init.astype(np.float32)
+        self.c64 = self.c32.astype(np.float64)
+        self.ns, self.f6 = self.o.fields_for(self.c64, f)
+        self.tb = self.o.tables(self.f6)
+        self.jobs = {}
+        for prec in (rbx.RBX_FP32, rbx.RBX_BF16):
+            j = rbx.Job()
+            j.set_geometry(self.g, precision=prec, weight_mode=weight_mode)
+            j.set_model(dev(self.c32))
+            self.jobs[prec] = j
+        t = self.tb
+        self.t32 = dict(T=t.T.astype(np.float32), a=t.a.astype(np.float32), gam=t.gam.astype(np.float32),
+                        K=t.K.astype(np.uint8), exits=t.exits.astype(np.float32))
+
+    def inject(self, job):
+        t = self.t32
+        job.set_tables(dev(t["T"]), dev(t["a"]), dev(t["gam"]), dev(t["K"], torch.uint8), dev(t["exits"]))
+
+
+@pytest.fixture(scope="module", params=["small", "ragged"])
+def case(request, oracle_mod):
+    if request.param == "small":
+        return Case(oracle_mod, P.small_two_disc(), 3e5)
+    return Case(oracle_mod, P.custom(50, 83, 1e-3, 36e-3, kind="discs", ny=77, freqs=(3e5,)), 3e5)
+
+
+def test_bf16_forward_identical_tables(case):
+    job = case.jobs[rbx.RBX_BF16]
+    case.inject(job)
+    rng = np.random.default_rng(7)
+    dm = (rng.standard_normal((case.g.ny, case.g.nx)) * 1e-9).astype(np.float32)
+    D = job.forward(case.f, dev(dm)).cpu().numpy()
+    w = 2 * math.pi * case.f
+    v = w * w * case.g.dx ** 2 * dm.astype(np.float64).ravel()[case.o.idx]
+    t = case.t32
+    D_orc = case.o.forward(case.f, t["T"].astype(np.float64), t["a"].astype(np.float64), t["K"].astype(np.int32), v)
+    assert rel_l2(D, D_orc) <= 5e-3
+    np.testing.assert_array_equal(D, D.T)
+
+
+@pytest.mark.parametrize("weight_mode", [0, 1])
+def test_bf16_backprojection_identical_tables(case, weight_mode, oracle_mod):
+    job = rbx.Job()
+    job.set_geometry(case.g, precision=rbx.RBX_BF16, weight_mode=weight_mode)
+    job.set_model(dev(case.c32))
+    case.inject(job)
+    o = oracle_mod.Oracle(case.g, weight_mode=weight_mode)
+    t = case.t32
+    T, a, gam = (t[k].astype(np.float64) for k in ("T", "a", "gam"))
+    dg = o.dgamma(gam, case.tb.cov)
+    rng = np.random.default_rng(11)
+    N = case.g.n_xducers
+    R = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+    out = job.adjoint(case.f, dev(R, torch.complex64), True).cpu().numpy()
+    ref = o.backproject(case.f, T, a, gam, t["K"].astype(np.int32), dg, R.astype(np.complex128))
+    assert rel_l2(out, ref) <= 5e-3
+    job.close()
+
+
+def test_bf16_update_matches_oracle(case):
+    w, o, f, df = case.w, case.o, case.f, 1e5
+    data, _ = o.predict(f, w.c_true)
+    c_ref, st_ref, bad = o.update_frequency(f, df, case.c64, data)
+    job = case.jobs[rbx.RBX_BF16]
+    job.set_model(dev(case.c32))
+    st = job.update_frequency(f, df, dev(data, torch.complex64))
+    c_gpu = job.get_model().cpu().numpy().astype(np.float64)
+    m = case.g.mask()
+    assert np.sqrt(np.mean((c_gpu[m] - c_ref[m]) ** 2)) <= 0.05
+    assert st["n_uncovered"] == 0
+
+
+def test_bf16_and_fp32_paths_agree(case):
+    """Same tables, same data: the BF16 and FP32 updates differ by far less than 0.05 m/s."""
+    w, o, f = case.w, case.o, case.f
+    data, _ = o.predict(f, w.c_true)
+    out = {}
+    for prec, job in case.jobs.items():
+        case.inject(job)
+        job.set_model(dev(case.c32))
+        job.update_from_tables(f, 1e5, dev(data, torch.complex64))
+        out[prec] = job.get_model().cpu().numpy().astype(np.float64)
+    m = case.g.mask()
+    d = out[rbx.RBX_BF16][m] - out[rbx.RBX_FP32][m]
+    dc = out[rbx.RBX_FP32][m] - case.c64[m]
+    assert np.sqrt(np.mean(d ** 2)) <= 0.01 * max(1.0, np.sqrt(np.mean(dc ** 2)))
