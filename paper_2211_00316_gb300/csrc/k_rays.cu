@@ -30,7 +30,7 @@ struct Fv {
 
 __device__ __forceinline__ void field_eval(const float *__restrict__ F, const RayParams &p, float px, float py, Fv &o)
 {
-    float u = (px - p.x0) / p.dx, v = (py - p.y0) / p.dx;
+    float u = (px - p.x0) * p.inv_dx, v = (py - p.y0) * p.inv_dx;
     int i = clampi_((int)floorf(u), 0, p.nx - 2), j = clampi_((int)floorf(v), 0, p.ny - 2);
     float tx = u - (float)i, ty = v - (float)j;
     const float4 *b = reinterpret_cast<const float4 *>(F) + ((size_t)j * p.nx + i) * 2;
@@ -49,7 +49,7 @@ __device__ __forceinline__ void field_eval(const float *__restrict__ F, const Ra
 // A ray sample as a triangle vertex.
 struct Vtx {
     float x, y, T, a, kx, ky;
-    int K, id;
+    int K;
 };
 
 __device__ __forceinline__ void cas128(unsigned long long *addr, unsigned long long clo, unsigned long long chi,
@@ -67,21 +67,14 @@ __device__ __forceinline__ void cas128(unsigned long long *addr, unsigned long l
         : "memory");
 }
 
-__device__ __forceinline__ void load128_cg(const unsigned long long *addr, unsigned long long &lo,
-                                           unsigned long long &hi)
-{
-    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(addr));
-}
-
-// Keep the entry with the smaller key. Each successful exchange lowers the stored key, so
-// the loop ends after at most as many rounds as there are competing triangles; the bound
-// only guards against a broken invariant and reports it.
-__device__ __forceinline__ void cas_min(TabEntry *e, unsigned long long key, unsigned long long pay,
-                                        unsigned long long *counters)
+// Keep the entry with the smaller key, starting from a known content (lo, hi) of the
+// entry. Every successful exchange lowers the stored key, so the loop ends after at most as
+// many rounds as there are competing triangles (the bound only reports a broken invariant).
+__device__ __forceinline__ void cas_min_from(TabEntry *e, unsigned long long key, unsigned long long pay,
+                                             unsigned long long lo, unsigned long long hi,
+                                             unsigned long long *counters)
 {
     unsigned long long *a = reinterpret_cast<unsigned long long *>(e);
-    unsigned long long lo, hi;
-    load128_cg(a, lo, hi);
     for (int it = 0; it < 1 << 16; ++it) {
         if (key >= lo) return;
         unsigned long long plo, phi;
@@ -93,54 +86,184 @@ __device__ __forceinline__ void cas_min(TabEntry *e, unsigned long long key, uns
     atomicAdd(&counters[3], 1ull);
 }
 
-// Edge function of P->Q at (px,py), evaluated from the vertex with the smaller id so that
-// the two triangles sharing an edge see exactly opposite values (watertight).
-__device__ __forceinline__ float edge_fn(const Vtx &P, const Vtx &Q, float px, float py)
+// One compare-and-swap in flight per lane. It is issued assuming the entry is untouched
+// (all ones, true for most nodes) and settled later: its result registers are first read
+// at the next flush, so the round trip overlaps the ray integration in between.
+struct PendingCas {
+    TabEntry *addr;
+    unsigned long long key, pay, lo, hi;
+    bool pend;
+};
+
+__device__ __forceinline__ void settle(PendingCas &q, unsigned long long *counters)
 {
-    if (P.id < Q.id) return __fmaf_rn(Q.x - P.x, py - P.y, -__fmul_rn(Q.y - P.y, px - P.x));
-    return -__fmaf_rn(P.x - Q.x, py - Q.y, -__fmul_rn(P.y - Q.y, px - Q.x));
+    if (!q.pend) return;
+    q.pend = false;
+    if (q.lo == ~0ull && q.hi == ~0ull) return;       // the entry was untouched: ours is stored
+    cas_min_from(q.addr, q.key, q.pay, q.lo, q.hi, counters);
 }
 
-__device__ void raster_tri(const Vtx &A, const Vtx &B, const Vtx &C, uint32_t tid, const RayParams &p,
-                           const int *__restrict__ node2x, TabEntry *fan, unsigned long long *counters)
+__device__ __forceinline__ void issue(PendingCas &q, TabEntry *addr, unsigned long long key, unsigned long long pay,
+                                      unsigned long long *counters)
 {
-    float ar = (B.x - A.x) * (C.y - A.y) - (B.y - A.y) * (C.x - A.x);
-    if (fabsf(ar) <= 1e-9f * p.ds * p.ds) return;  // degenerate
-    float minx = fminf(A.x, fminf(B.x, C.x)), maxx = fmaxf(A.x, fmaxf(B.x, C.x));
-    float miny = fminf(A.y, fminf(B.y, C.y)), maxy = fmaxf(A.y, fmaxf(B.y, C.y));
-    int ix0 = max(0, (int)ceilf((minx - p.x0) / p.dx)), ix1 = min(p.nx - 1, (int)floorf((maxx - p.x0) / p.dx));
-    int iy0 = max(0, (int)ceilf((miny - p.y0) / p.dx)), iy1 = min(p.ny - 1, (int)floorf((maxy - p.y0) / p.dx));
-    for (int iy = iy0; iy <= iy1; iy++) {
-        float py = p.y0 + (float)iy * p.dx;
-        for (int ix = ix0; ix <= ix1; ix++) {
-            int xi = __ldg(&node2x[iy * p.nx + ix]);
-            if (xi < 0) continue;
-            float px = p.x0 + (float)ix * p.dx;
-            float eA = edge_fn(B, C, px, py), eB = edge_fn(C, A, px, py), eC = edge_fn(A, B, px, py);
-            float sum = eA + eB + eC;
-            bool in = sum > 0.f ? (eA >= 0.f && eB >= 0.f && eC >= 0.f) : (eA <= 0.f && eB <= 0.f && eC <= 0.f);
-            if (!in || sum == 0.f) continue;
-            float lb = eB / sum, lc = eC / sum, la = eA / sum;
-            float T = A.T + lb * (B.T - A.T) + lc * (C.T - A.T);
-            float a = la * A.a + lb * B.a + lc * C.a;
-            float kx = la * A.kx + lb * B.kx + lc * C.kx, ky = la * A.ky + lb * B.ky + lc * C.ky;
-            float gam = atan2f(ky, kx);
-            int K = max(A.K, max(B.K, C.K));
-            unsigned long long key = ((unsigned long long)__float_as_uint(T) << 32) | ((unsigned long long)tid << 8) |
-                                     (unsigned long long)min(K, 255);
-            unsigned long long pay = ((unsigned long long)__float_as_uint(gam) << 32) | __float_as_uint(a);
-            cas_min(&fan[xi], key, pay, counters);
+    settle(q, counters);
+    q.addr = addr;
+    q.key = key;
+    q.pay = pay;
+    cas128(reinterpret_cast<unsigned long long *>(addr), ~0ull, ~0ull, key, pay, q.lo, q.hi);
+    q.pend = true;
+}
+
+// Per-warp queue of table hits in shared memory, drained 32 at a time (one per lane):
+// node, key, and the interpolated amplitude and direction (the direction angle is formed
+// at the drain, where all 32 lanes are busy).
+struct HitQueue {
+    int *xi;
+    unsigned long long *key;
+    float4 *v;   // (a, kappa_x, kappa_y, -)
+    int n;       // warp-uniform
+};
+
+__device__ __forceinline__ void drain_one(const HitQueue &hq, int q, TabEntry *fan, PendingCas &pc,
+                                          unsigned long long *counters)
+{
+    const float4 v = hq.v[q];
+    const unsigned long long pay = ((unsigned long long)__float_as_uint(atan2f(v.z, v.y)) << 32) | __float_as_uint(v.x);
+    issue(pc, fan + hq.xi[q], hq.key[q], pay, counters);
+}
+
+// Edge function of P -> Q at (px, py), always evaluated from the vertex with the smaller
+// id (ids order P[j,i] < P[j,i+1] < P[j+1,i] < P[j+1,i+1]), so the triangles on both sides
+// of an edge see exactly opposite values and no node falls between them.
+__device__ __forceinline__ float edge_fn(const Vtx &P, const Vtx &Q, float px, float py)
+{
+    return __fmaf_rn(Q.x - P.x, py - P.y, -__fmul_rn(Q.y - P.y, px - P.x));
+}
+
+__device__ __forceinline__ bool tri_inside(float eA, float eB, float eC, float &sum)
+{
+    sum = eA + eB + eC;
+    bool in = sum > 0.f ? (eA >= 0.f && eB >= 0.f && eC >= 0.f) : (eA <= 0.f && eB <= 0.f && eC <= 0.f);
+    return in && sum != 0.f;
+}
+
+__device__ __forceinline__ unsigned long long tri_key(const Vtx &A, const Vtx &B, const Vtx &C, float lb, float lc,
+                                                      uint32_t tid)
+{
+    float T = A.T + lb * (B.T - A.T) + lc * (C.T - A.T);
+    int K = max(A.K, max(B.K, C.K));
+    return ((unsigned long long)__float_as_uint(T) << 32) | ((unsigned long long)tid << 8) |
+           (unsigned long long)min(K, 255);
+}
+
+// Rasterise the ray-tube quad P00 = P[j,i], P01 = P[j,i+1], P10 = P[j+1,i], P11 = P[j+1,i+1]
+// of every valid lane as triangles t0 = (P00, P10, P11) and t1 = (P00, P11, P01) (ids
+// tid0, tid0 + 1). Called by the whole warp. A node inside both triangles (on the shared
+// diagonal) keeps the smaller key locally; hits go to the warp's queue. rows[iy] gives the
+// mask nodes of grid row iy: (first compact index, first ix, last ix).
+__device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, const Vtx &P01, const Vtx &P10,
+                                                 const Vtx &P11, uint32_t tid0, const RayParams &p, float inv_dx,
+                                                 const int4 *rows, TabEntry *fan, HitQueue &hq, PendingCas &pc,
+                                                 unsigned long long *counters)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    bool ok0 = false, ok1 = false;
+    int ix0 = 0, iy0 = 0, w = 0, cnt = 0;
+    if (valid) {
+        const float tiny = 1e-9f * p.ds * p.ds;
+        const float ar0 = (P10.x - P00.x) * (P11.y - P00.y) - (P10.y - P00.y) * (P11.x - P00.x);
+        const float ar1 = (P11.x - P00.x) * (P01.y - P00.y) - (P11.y - P00.y) * (P01.x - P00.x);
+        ok0 = fabsf(ar0) > tiny;
+        ok1 = fabsf(ar1) > tiny;
+        if (ok0 || ok1) {
+            float minx = fminf(fminf(P00.x, P01.x), fminf(P10.x, P11.x));
+            float maxx = fmaxf(fmaxf(P00.x, P01.x), fmaxf(P10.x, P11.x));
+            float miny = fminf(fminf(P00.y, P01.y), fminf(P10.y, P11.y));
+            float maxy = fmaxf(fmaxf(P00.y, P01.y), fmaxf(P10.y, P11.y));
+            ix0 = max(0, (int)ceilf((minx - p.x0) * inv_dx));
+            int ix1 = min(p.nx - 1, (int)floorf((maxx - p.x0) * inv_dx));
+            iy0 = max(0, (int)ceilf((miny - p.y0) * inv_dx));
+            int iy1 = min(p.ny - 1, (int)floorf((maxy - p.y0) * inv_dx));
+            w = ix1 - ix0 + 1;
+            int h = iy1 - iy0 + 1;
+            cnt = (w > 0 && h > 0) ? w * h : 0;
+        }
+    }
+    int ix = ix0, iy = iy0;
+    for (int it = 0; __any_sync(FULL, it < cnt); it++) {
+        bool hit = false;
+        int xi = 0;
+        unsigned long long key = ~0ull;
+        float4 hv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (it < cnt) {
+            const int4 ro = rows[iy];
+            if (ix >= ro.y && ix <= ro.z) {
+                xi = ro.x + ix - ro.y;
+                const float px = p.x0 + (float)ix * p.dx, py = p.y0 + (float)iy * p.dx;
+                const float e1 = edge_fn(P00, P10, px, py), e2 = edge_fn(P10, P11, px, py);
+                const float e3 = edge_fn(P00, P11, px, py), e4 = edge_fn(P01, P11, px, py);
+                const float e5 = edge_fn(P00, P01, px, py);
+                float s0, s1, lb0 = 0.f, lc0 = 0.f, lb1 = 0.f, lc1 = 0.f;
+                unsigned long long k0 = ~0ull, k1 = ~0ull;
+                if (ok0 && tri_inside(e2, -e3, e1, s0)) {
+                    float inv = 1.f / s0;
+                    lb0 = -e3 * inv;
+                    lc0 = e1 * inv;
+                    k0 = tri_key(P00, P10, P11, lb0, lc0, tid0);
+                }
+                if (ok1 && tri_inside(-e4, -e5, e3, s1)) {
+                    float inv = 1.f / s1;
+                    lb1 = -e5 * inv;
+                    lc1 = e3 * inv;
+                    k1 = tri_key(P00, P11, P01, lb1, lc1, tid0 + 1);
+                }
+                if (k0 != ~0ull || k1 != ~0ull) {
+                    const bool use0 = k0 < k1;
+                    const float lb = use0 ? lb0 : lb1, lc = use0 ? lc0 : lc1, la = 1.f - lb - lc;
+                    const float Ba = use0 ? P10.a : P11.a, Ca = use0 ? P11.a : P01.a;
+                    const float Bkx = use0 ? P10.kx : P11.kx, Ckx = use0 ? P11.kx : P01.kx;
+                    const float Bky = use0 ? P10.ky : P11.ky, Cky = use0 ? P11.ky : P01.ky;
+                    hv = make_float4(la * P00.a + lb * Ba + lc * Ca, la * P00.kx + lb * Bkx + lc * Ckx,
+                                     la * P00.ky + lb * Bky + lc * Cky, 0.f);
+                    key = use0 ? k0 : k1;
+                    hit = true;
+                }
+            }
+            if (++ix >= ix0 + w) { ix = ix0; iy++; }
+        }
+        const unsigned b = __ballot_sync(FULL, hit);
+        if (b) {
+            const int slot = hq.n + __popc(b & ((1u << lane) - 1));
+            if (hit) {
+                hq.xi[slot] = xi;
+                hq.key[slot] = key;
+                hq.v[slot] = hv;
+            }
+            hq.n += __popc(b);
+            __syncwarp();
+            if (hq.n >= 32) {
+                drain_one(hq, hq.n - 32 + lane, fan, pc, counters);
+                hq.n -= 32;
+                __syncwarp();
+            }
         }
     }
 }
 
-__global__ __launch_bounds__(128) void k_trace_raster(const float *__restrict__ F, const int *__restrict__ node2x,
-                                                      TabEntry *__restrict__ tab, float4 *__restrict__ exits,
-                                                      RayParams p, unsigned long long *counters)
+__global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict__ F, const int4 *__restrict__ rows_g,
+                                                         TabEntry *__restrict__ tab, float4 *__restrict__ exits,
+                                                         RayParams p, unsigned long long *counters)
 {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    extern __shared__ int4 rows[];                          // [ny] mask row ranges
+    __shared__ int q_xi[4][64];
+    __shared__ unsigned long long q_key[4][64];
+    __shared__ float4 q_v[4][64];
+    for (int q = threadIdx.x; q < p.ny; q += blockDim.x) rows[q] = rows_g[q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
     const int e = blockIdx.y;
     const int N = p.N;
     const int nwarps = (N - 2 + 30) / 31;
@@ -148,69 +271,74 @@ __global__ __launch_bounds__(128) void k_trace_raster(const float *__restrict__ 
     const int j = 1 + 31 * warp + lane;      // this lane's ray
     const bool has_ray = j <= N - 1;
     TabEntry *fan = tab + (size_t)e * p.X;
+    const float ds = p.ds, hds = 0.5f * p.ds, inv_dx = p.inv_dx, R2 = p.R * p.R;
+    HitQueue hq{q_xi[wib], q_key[wib], q_v[wib], 0};
+    PendingCas pc{};
+    pc.pend = false;
 
     const double be = 2.0 * 3.14159265358979323846 * e / N;
-    const float xe = (float)(p.R * cos(be)), ye = (float)(p.R * sin(be));
+    float x = (float)(p.R * cos(be)), y = (float)(p.R * sin(be));
     const float gam0 = (float)(be + 3.14159265358979323846 / 2 + 3.14159265358979323846 * j / N);
 
-    // reference and paraxial ray state
-    float x = xe, y = ye, px, py, dxx = 0.f, dxy = 0.f, dpx, dpy, T = 0.f, Tc = 0.f;
-    float J1 = 0.f, n1 = 0.f, Jlast = 0.f;
-    int K = 0;
+    // reference ray (x, p) and paraxial ray (dx, dp); F1 caches the fields at x
+    Fv F1;
+    field_eval(F, p, x, y, F1);
+    float px, py, dpx, dpy, dxx = 0.f, dxy = 0.f, T = 0.f, Tc = 0.f;
     {
-        Fv f0;
-        field_eval(F, p, x, y, f0);
         float s0, c0;
         sincosf(gam0, &s0, &c0);
-        px = f0.n * c0; py = f0.n * s0;
-        dpx = -f0.n * s0; dpy = f0.n * c0;
+        px = F1.n * c0; py = F1.n * s0;
+        dpx = -F1.n * s0; dpy = F1.n * c0;
     }
+    float sc1 = 0.f, Jlast = 0.f;   // sc1 = sqrt(n_1 |J_1| / ds): a_i = sc1 / sqrt(n_i |J_i|)
+    int K = 0;
     bool alive = has_ray;
     Vtx prev{}, nprev{};
-    const float ds = p.ds;
 
     for (int i = 0; i < p.maxs; i++) {
         Vtx cur{};
         bool have = false;
         if (alive) {
-            Fv F1, F2, F3;
-            field_eval(F, p, x, y, F1);
-            float n = F1.n;
-            float pn = sqrtf(px * px + py * py);
-            px *= n / pn; py *= n / pn;
-            float qx = px / n, qy = py / n, qpx = F1.gx, qpy = F1.gy;
-            float xa = x + ds * qx, ya = y + ds * qy;
-            field_eval(F, p, xa, ya, F2);
-            float pax = px + ds * qpx, pay = py + ds * qpy;
-            float pan = sqrtf(pax * pax + pay * pay);
-            pax *= F2.n / pan; pay *= F2.n / pan;
-            float qax = pax / F2.n, qay = pay / F2.n, qpax = F2.gx, qpay = F2.gy;
-            float sx = qx + qax, sy = qy + qay, sn = sqrtf(sx * sx + sy * sy);
-            float dirx = sx / sn, diry = sy / sn;
+            // stage 1 at x: normalise p to n(x), q_x = p/n, q_p = grad n
+            const float n = F1.n, in = 1.f / n;
+            const float sc = n * rsqrtf(px * px + py * py);
+            px *= sc; py *= sc;
+            const float qx = px * in, qy = py * in;
+            // stage 2 at the auxiliary point x + ds q_x
+            Fv F2;
+            field_eval(F, p, x + ds * qx, y + ds * qy, F2);
+            const float na = F2.n, ina = 1.f / na;
+            float pax = px + ds * F1.gx, pay = py + ds * F1.gy;
+            const float sca = na * rsqrtf(pax * pax + pay * pay);
+            pax *= sca; pay *= sca;
+            const float qax = pax * ina, qay = pay * ina;
+            const float sx = qx + qax, sy = qy + qay, rs = rsqrtf(sx * sx + sy * sy);
+            const float dirx = sx * rs, diry = sy * rs;
             float xn = x + ds * dirx, yn = y + ds * diry;
-            float pxn = px + ds * (qpx + qpax) * 0.5f, pyn = py + ds * (qpy + qpay) * 0.5f;
-            // paraxial system, both stages at the reference ray's stage values
-            float n2 = n * n;
-            float gd = F1.gx * dxx + F1.gy * dxy, pd = px * dpx + py * dpy;
-            float qdxx = -px * gd / n2 + dpx / n, qdxy = -py * gd / n2 + dpy / n;
-            float qdpx = F1.hxx * dxx + F1.hxy * dxy - F1.gx * gd / n + F1.gx * pd / n2;
-            float qdpy = F1.hxy * dxx + F1.hyy * dxy - F1.gy * gd / n + F1.gy * pd / n2;
-            float dpax = dpx + ds * qdpx, dpay = dpy + ds * qdpy;
-            float dxax = dxx + ds * qdxx, dxay = dxy + ds * qdxy;
-            float na = F2.n, na2 = na * na;
-            float gda = F2.gx * dxax + F2.gy * dxay, pda = pax * dpax + pay * dpay;
-            float qdxax = -pax * gda / na2 + dpax / na, qdxay = -pay * gda / na2 + dpay / na;
-            float qdpax = F2.hxx * dxax + F2.hxy * dxay - F2.gx * gda / na + F2.gx * pda / na2;
-            float qdpay = F2.hxy * dxax + F2.hyy * dxay - F2.gy * gda / na + F2.gy * pda / na2;
-            float dxxn = dxx + ds * (qdxx + qdxax) * 0.5f, dxyn = dxy + ds * (qdxy + qdxay) * 0.5f;
-            float dpxn = dpx + ds * (qdpx + qdpax) * 0.5f, dpyn = dpy + ds * (qdpy + qdpay) * 0.5f;
-            field_eval(F, p, xn, yn, F3);
-            float inc = ds * (n + F3.n) * 0.5f;
-            bool last = xn * xn + yn * yn >= p.R * p.R;
+            float pxn = px + hds * (F1.gx + F2.gx), pyn = py + hds * (F1.gy + F2.gy);
+            // paraxial system, both stages at the reference ray's stage values:
+            // q_dx = (dp - p (g.dx)/n)/n, q_dp = H dx + g ((p.dp)/n - g.dx)/n
+            const float gd = F1.gx * dxx + F1.gy * dxy, pd = px * dpx + py * dpy;
+            const float qdxx = in * (dpx - px * gd * in), qdxy = in * (dpy - py * gd * in);
+            const float w1 = in * (pd * in - gd);
+            const float qdpx = F1.hxx * dxx + F1.hxy * dxy + F1.gx * w1;
+            const float qdpy = F1.hxy * dxx + F1.hyy * dxy + F1.gy * w1;
+            const float dpax = dpx + ds * qdpx, dpay = dpy + ds * qdpy;
+            const float dxax = dxx + ds * qdxx, dxay = dxy + ds * qdxy;
+            const float gda = F2.gx * dxax + F2.gy * dxay, pda = pax * dpax + pay * dpay;
+            const float qdxax = ina * (dpax - pax * gda * ina), qdxay = ina * (dpay - pay * gda * ina);
+            const float w2 = ina * (pda * ina - gda);
+            const float qdpax = F2.hxx * dxax + F2.hxy * dxay + F2.gx * w2;
+            const float qdpay = F2.hxy * dxax + F2.hyy * dxay + F2.gy * w2;
+            float dxxn = dxx + hds * (qdxx + qdxax), dxyn = dxy + hds * (qdxy + qdxay);
+            float dpxn = dpx + hds * (qdpx + qdpax), dpyn = dpy + hds * (qdpy + qdpay);
+            field_eval(F, p, xn, yn, F2);                // fields at the new sample (reused next step)
+            float inc = hds * (n + F2.n);
+            const bool last = xn * xn + yn * yn >= R2;
             if (last) {
-                // final partial step: crossing of the step's chord with the ring; other
+                // final partial step: crossing of the step's chord with the ring; the other
                 // quantities interpolated linearly along the chord
-                float b = x * dirx + y * diry, cc = x * x + y * y - p.R * p.R;
+                float b = x * dirx + y * diry, cc = x * x + y * y - R2;
                 float disc = b * b - cc;
                 float t = -b + sqrtf(disc > 0.f ? disc : 0.f);
                 t = fminf(fmaxf(t, 0.f), ds);
@@ -220,23 +348,22 @@ __global__ __launch_bounds__(128) void k_trace_raster(const float *__restrict__ 
                 dxxn = dxx + fr * (dxxn - dxx); dxyn = dxy + fr * (dxyn - dxy);
                 dpxn = dpx + fr * (dpxn - dpx); dpyn = dpy + fr * (dpyn - dpy);
                 pxn = px + fr * (pxn - px); pyn = py + fr * (pyn - py);
-                field_eval(F, p, xn, yn, F3);
+                field_eval(F, p, xn, yn, F2);
             }
-            // compensated travel-time sum (trapezoid of n along the samples)
-            {
+            {   // compensated travel-time sum (trapezoid of n along the samples)
                 float yk = inc - Tc, tk = T + yk;
                 Tc = (tk - T) - yk;
                 T = tk;
             }
             x = xn; y = yn; px = pxn; py = pyn; dxx = dxxn; dxy = dxyn; dpx = dpxn; dpy = dpyn;
-            float pm = sqrtf(px * px + py * py), tx = px / pm, ty = py / pm;
-            float J = dxx * ty - dxy * tx;
-            if (i == 0) { J1 = J; n1 = F3.n; Jlast = J; }
+            F1 = F2;
+            const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
+            const float J = dxx * ty - dxy * tx;
+            if (i == 0) { sc1 = sqrtf(F1.n * fabsf(J) / ds); Jlast = J; }
             else if (J * Jlast < 0.f) K++;   // caustic: sign change of the ray Jacobian
             if (J != 0.f) Jlast = J;
             cur.x = x; cur.y = y; cur.T = T; cur.kx = tx; cur.ky = ty; cur.K = K;
-            cur.a = sqrtf((n1 / F3.n) * fabsf(J1 / J) / ds);
-            cur.id = j * 4096 + (i + 1);
+            cur.a = sc1 * rsqrtf(F1.n * fabsf(J));
             have = true;
             if (last) {
                 alive = false;
@@ -253,26 +380,48 @@ __global__ __launch_bounds__(128) void k_trace_raster(const float *__restrict__ 
         ncur.kx = __shfl_down_sync(FULL, cur.kx, 1);
         ncur.ky = __shfl_down_sync(FULL, cur.ky, 1);
         ncur.K = __shfl_down_sync(FULL, cur.K, 1);
-        ncur.id = __shfl_down_sync(FULL, cur.id, 1);
-        bool nhave = __shfl_down_sync(FULL, (int)have, 1) != 0;
-        if (i >= 1 && have && nhave && lane < 31 && j + 1 <= N - 1) {
-            uint32_t base = ((uint32_t)j << 11 | (uint32_t)i) << 1;   // 24-bit id, order (j, i, which)
-            raster_tri(prev, nprev, ncur, base, p, node2x, fan, counters);
-            raster_tri(prev, ncur, cur, base + 1, p, node2x, fan, counters);
-        }
+        const bool nhave = __shfl_down_sync(FULL, (int)have, 1) != 0;
+        const bool valid = i >= 1 && have && nhave && lane < 31 && j + 1 <= N - 1;
+        raster_quad_warp(valid, prev, cur, nprev, ncur, ((uint32_t)j << 11 | (uint32_t)i) << 1, p, inv_dx, rows, fan,
+                         hq, pc, counters);
         prev = cur;
         nprev = ncur;
         if (!__any_sync(FULL, alive)) break;
         if (i == p.maxs - 1 && alive) atomicAdd(&counters[2], 1ull);   // ray never reached the ring
     }
+    // drain the queue and settle every exchange still in flight
+    if (lane < hq.n) drain_one(hq, lane, fan, pc, counters);
+    settle(pc, counters);
 }
 
-void launch_trace_raster(const float *fields, const int *node2x, TabEntry *tab, float4 *exits, const RayParams &p,
+void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
                          unsigned long long *counters, cudaStream_t s)
 {
     int nwarps = (p.N - 2 + 30) / 31;
     dim3 grd((nwarps + 3) / 4, p.N);
-    k_trace_raster<<<grd, 128, 0, s>>>(fields, node2x, tab, exits, p, counters);
+    k_trace_raster<<<grd, 128, (size_t)p.ny * sizeof(int4), s>>>(fields, rows, tab, exits, p, counters);
+}
+
+// rows[iy] = (compact index of the row's first mask node, first ix, last ix); empty rows
+// get first ix > last ix. The mask is a disc, so each row's mask nodes are contiguous.
+__global__ void k_mask_rows(const int *__restrict__ node2x, int nx, int ny, int4 *__restrict__ rows)
+{
+    int iy = blockIdx.x * blockDim.x + threadIdx.x;
+    if (iy >= ny) return;
+    int first = -1, last = -2, off = 0;
+    for (int ix = 0; ix < nx; ix++) {
+        int k = node2x[iy * nx + ix];
+        if (k >= 0) {
+            if (first < 0) { first = ix; off = k; }
+            last = ix;
+        }
+    }
+    rows[iy] = make_int4(off, first < 0 ? 1 : first, first < 0 ? 0 : last, 0);
+}
+
+void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s)
+{
+    k_mask_rows<<<(ny + 127) / 128, 128, 0, s>>>(node2x, nx, ny, rows);
 }
 
 // ---------------------------------------------------------------- a4

@@ -65,7 +65,7 @@ static cudaError_t dalloc(T *&p, size_t n)
 
 static void free_ws(Workspace &w)
 {
-    void *ps[] = {w.node2x, w.idx, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
+    void *ps[] = {w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
                   w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -189,6 +189,7 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     w.fwd_splits = forward_splits(w.N, X);
     const size_t NX = N * (size_t)X;
     ALLOC(w.idx, X);
+    ALLOC(w.rows, (size_t)g.ny);
     ALLOC(w.c, nxy);
     ALLOC(w.ns, nxy);
     ALLOC(w.ns64, nxy);
@@ -222,8 +223,9 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     ALLOC(w.counters, 8);
 #undef ALLOC
     launch_mask_idx(w.node2x, (int)nxy, w.idx, j->stream);
+    launch_mask_rows(w.node2x, g.nx, g.ny, w.rows, j->stream);
     launch_fill(w.c, (float)g.c0, nxy, j->stream);
-    LAUNCHED(j, 2);
+    LAUNCHED(j, 3);
     CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 8 * sizeof(unsigned long long), j->stream));
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     j->g = g;
@@ -296,9 +298,9 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     RayParams p;
     p.N = w.N; p.X = w.X; p.nx = w.nx; p.ny = w.ny;
     p.dx = (float)j->g.dx; p.x0 = (float)j->g.x0; p.y0 = (float)j->g.y0;
-    p.R = (float)j->g.ring_radius; p.ds = (float)j->g.ds;
+    p.R = (float)j->g.ring_radius; p.ds = (float)j->g.ds; p.inv_dx = (float)(1.0 / j->g.dx);
     p.maxs = max_steps(j->g);
-    launch_trace_raster(w.fields, w.node2x, w.tab, w.exits, p, w.counters, j->stream);
+    launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->stream);
     LAUNCHED(j, 1);
     if ((st = record(j, EV_TRACE))) return st;
     launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);

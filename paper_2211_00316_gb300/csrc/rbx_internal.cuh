@@ -25,7 +25,7 @@ struct __align__(16) TabEntry {
 
 struct RayParams {
     int N, X, nx, ny;
-    float dx, x0, y0, R, ds;
+    float dx, x0, y0, R, ds, inv_dx;
     int maxs;
 };
 
@@ -48,6 +48,7 @@ struct TcPlanes {
 struct Workspace {
     int N = 0, X = 0, nx = 0, ny = 0;
     int *node2x = nullptr, *idx = nullptr;
+    int4 *rows = nullptr;       // per grid row: (compact index of first mask node, first ix, last ix)
     float *c = nullptr, *ns = nullptr, *tmp = nullptr, *fields = nullptr;
     double *ns64 = nullptr, *tmp64 = nullptr;
     TabEntry *tab = nullptr;
@@ -73,8 +74,9 @@ void launch_check_model(const float *c, int n, unsigned long long *flag, cudaStr
 void launch_fill(float *p, float v, size_t n, cudaStream_t s);
 
 // k_rays.cu
-void launch_trace_raster(const float *fields, const int *node2x, TabEntry *tab, float4 *exits, const RayParams &p,
+void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
                          unsigned long long *counters, cudaStream_t s);
+void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s);
 void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, unsigned long long *counters, cudaStream_t s);
 void launch_direct_green(const float4 *exits, int N, double f, double c0, float2 *g, unsigned long long *counters,
                          cudaStream_t s);
