@@ -214,7 +214,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rbx", choices=["rbx", "reference"])
     ap.add_argument("--workload", default="precision_ring1024", choices=["precision_ring1024", "fp32_ring256", "small"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "bf16x3"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -51,12 +51,16 @@ __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 
 // ---------------------------------------------------------------- forward
 
-__global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ CUtensorMap mGre,
-                                                       const __grid_constant__ CUtensorMap mGim,
-                                                       const __grid_constant__ CUtensorMap mGvre,
-                                                       const __grid_constant__ CUtensorMap mGvim, int N, int ntile,
-                                                       int nk, int kper, float2 *__restrict__ part,
-                                                       unsigned *__restrict__ err)
+// Operand maps of one K pass: A (re, im) and B (re, im).
+struct Maps4 {
+    CUtensorMap are, aim, bre, bim;
+};
+
+// passes = 1: A_hi B_hi. passes = 3 (split BF16): A_hi B_hi + A_hi B_lo + A_lo B_hi, all
+// accumulated into the same tensor-memory accumulators.
+__global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ Maps4 hi, const __grid_constant__ Maps4 lo,
+                                                       int passes, int N, int ntile, int nk, int kper,
+                                                       float2 *__restrict__ part, unsigned *__restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *tiles = align1024(smem_raw);
@@ -71,6 +75,7 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ C
     const int tr = te + b;
     const int split = blockIdx.y;
     const int c0 = split * kper, nc = min(nk, c0 + kper) - c0;
+    const int ntot = passes * nc;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < F_STAGES; s++) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
@@ -84,18 +89,20 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ C
     const uint32_t tmem = *tslot;
 
     if (warp == 0 && lane == 0) {
-        prefetch_tmap(&mGre); prefetch_tmap(&mGim); prefetch_tmap(&mGvre); prefetch_tmap(&mGvim);
+        prefetch_tmap(&hi.are); prefetch_tmap(&hi.aim); prefetch_tmap(&hi.bre); prefetch_tmap(&hi.bim);
         int issued = 0;
-        for (int c = 0; c < nc; c++) {
+        for (int c = 0; c < ntot; c++) {
             int s = c % F_STAGES;
             if (c >= F_STAGES && !mbar_wait(empty + s, ((c / F_STAGES) - 1) & 1)) { atomicOr(err, 1u); break; }
             mbar_arrive_expect_tx(full + s, F_TILES * TILE);
             uint32_t base = smem_u32(tiles + (size_t)s * F_TILES * TILE);
-            int kx = (c0 + c) * BK;
-            tma_load_2d(base, &mGre, full + s, kx, te * BM);
-            tma_load_2d(base + TILE, &mGim, full + s, kx, te * BM);
-            tma_load_2d(base + 2 * TILE, &mGvre, full + s, kx, tr * BN);
-            tma_load_2d(base + 3 * TILE, &mGvim, full + s, kx, tr * BN);
+            const int pass = c / nc;
+            const Maps4 &A = pass == 2 ? lo : hi, &B = pass == 1 ? lo : hi;
+            int kx = (c0 + c - pass * nc) * BK;
+            tma_load_2d(base, &A.are, full + s, kx, te * BM);
+            tma_load_2d(base + TILE, &A.aim, full + s, kx, te * BM);
+            tma_load_2d(base + 2 * TILE, &B.bre, full + s, kx, tr * BN);
+            tma_load_2d(base + 3 * TILE, &B.bim, full + s, kx, tr * BN);
             issued++;
         }
         // no copy may still be in flight when the CTA retires
@@ -105,7 +112,7 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ C
         if (lane == 0) {
             const uint32_t ip = idesc_bf16(BM, BN, 0), in = idesc_bf16(BM, BN, 1);
             const uint32_t dre = tmem, dim = tmem + BN;
-            for (int c = 0; c < nc; c++) {
+            for (int c = 0; c < ntot; c++) {
                 int s = c % F_STAGES;
                 if (!mbar_wait(full + s, (c / F_STAGES) & 1)) { atomicOr(err, 2u); break; }
                 fence_after();
@@ -161,12 +168,18 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ C
 
 // ---------------------------------------------------------------- back-projection
 
-__global__ __launch_bounds__(192, 1) void k_backproject_tc(
-    const __grid_constant__ CUtensorMap mUre, const __grid_constant__ CUtensorMap mUim,
-    const __grid_constant__ CUtensorMap mVre, const __grid_constant__ CUtensorMap mVim,
-    const __grid_constant__ CUtensorMap mRre, const __grid_constant__ CUtensorMap mRim,
-    const __nv_bfloat16 *__restrict__ planes, size_t pstride, int Npad, int nk, float sgn, float2 *__restrict__ bpart,
-    int Xp, unsigned *__restrict__ err)
+// Operand maps of one K pass: A = u and conj(kappa) u (re, im), B = R_s (re, im).
+struct Maps6 {
+    CUtensorMap ure, uim, vre, vim, rre, rim;
+};
+
+// passes = 1: A_hi B_hi; passes = 3 (split BF16) adds A_hi B_lo and A_lo B_hi, and the
+// epilogue weights are read as hi + lo.
+__global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant__ Maps6 hi,
+                                                           const __grid_constant__ Maps6 lo, int passes,
+                                                           const __nv_bfloat16 *__restrict__ planes, size_t pstride,
+                                                           int Npad, int nk, float sgn, float2 *__restrict__ bpart,
+                                                           int Xp, unsigned *__restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *tiles = align1024(smem_raw);
@@ -189,21 +202,24 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(
     const uint32_t tmem = *tslot;
 
     if (warp == 0 && lane == 0) {
-        prefetch_tmap(&mUre); prefetch_tmap(&mUim); prefetch_tmap(&mVre); prefetch_tmap(&mVim);
-        prefetch_tmap(&mRre); prefetch_tmap(&mRim);
+        prefetch_tmap(&hi.ure); prefetch_tmap(&hi.uim); prefetch_tmap(&hi.vre); prefetch_tmap(&hi.vim);
+        prefetch_tmap(&hi.rre); prefetch_tmap(&hi.rim);
+        const int ntot = passes * nk;
         int issued = 0;
-        for (int c = 0; c < nk; c++) {
+        for (int c = 0; c < ntot; c++) {
             int s = c % B_STAGES;
             if (c >= B_STAGES && !mbar_wait(empty + s, ((c / B_STAGES) - 1) & 1)) { atomicOr(err, 1u); break; }
             mbar_arrive_expect_tx(full + s, B_TILES * TILE);
             uint32_t base = smem_u32(tiles + (size_t)s * B_TILES * TILE);
-            int kx = c * BK;
-            tma_load_2d(base, &mUre, full + s, kx, xt * BM);
-            tma_load_2d(base + TILE, &mUim, full + s, kx, xt * BM);
-            tma_load_2d(base + 2 * TILE, &mVre, full + s, kx, xt * BM);
-            tma_load_2d(base + 3 * TILE, &mVim, full + s, kx, xt * BM);
-            tma_load_2d(base + 4 * TILE, &mRre, full + s, kx, et * BN);
-            tma_load_2d(base + 5 * TILE, &mRim, full + s, kx, et * BN);
+            const int pass = c / nk;
+            const Maps6 &A = pass == 2 ? lo : hi, &B = pass == 1 ? lo : hi;
+            int kx = (c - pass * nk) * BK;
+            tma_load_2d(base, &A.ure, full + s, kx, xt * BM);
+            tma_load_2d(base + TILE, &A.uim, full + s, kx, xt * BM);
+            tma_load_2d(base + 2 * TILE, &A.vre, full + s, kx, xt * BM);
+            tma_load_2d(base + 3 * TILE, &A.vim, full + s, kx, xt * BM);
+            tma_load_2d(base + 4 * TILE, &B.rre, full + s, kx, et * BN);
+            tma_load_2d(base + 5 * TILE, &B.rim, full + s, kx, et * BN);
             issued++;
         }
         for (int c = (issued > B_STAGES ? issued - B_STAGES : 0); c < issued; c++)
@@ -212,7 +228,8 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(
         if (lane == 0) {
             const uint32_t ip = idesc_bf16(BM, BN, 0), in = idesc_bf16(BM, BN, 1);
             const uint32_t p0r = tmem, p0i = tmem + BN, p1r = tmem + 2 * BN, p1i = tmem + 3 * BN;
-            for (int c = 0; c < nk; c++) {
+            const int ntot = passes * nk;
+            for (int c = 0; c < ntot; c++) {
                 int s = c % B_STAGES;
                 if (!mbar_wait(full + s, (c / B_STAGES) & 1)) { atomicOr(err, 2u); break; }
                 fence_after();
@@ -246,9 +263,11 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(
         float gre = 0.f, gim = 0.f;
         if (ok) {
             const uint32_t lanes = (uint32_t)(sub * 32) << 16;
-            // epilogue weights at [x][e]: u (planes 0, 1) and kappa u (planes 4, 5)
+            // epilogue weights at [x][e]: u (planes 0, 1) and kappa u (planes 4, 5); with
+            // split BF16 the lo parts are planes 6 + (0, 1, 4, 5)
             const __nv_bfloat16 *w0r = planes + (size_t)x * Npad + et * BN;
             const __nv_bfloat16 *w0i = w0r + pstride, *w1r = w0r + 4 * pstride, *w1i = w0r + 5 * pstride;
+            const size_t lo_off = 6 * pstride;
 #pragma unroll 1
             for (int cc = 0; cc < BN; cc += 32) {
                 float a0r[32], a0i[32], a1r[32], a1i[32];
@@ -262,14 +281,30 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(
                     uint4 i0 = *reinterpret_cast<const uint4 *>(w0i + cc + 8 * q);
                     uint4 r1 = *reinterpret_cast<const uint4 *>(w1r + cc + 8 * q);
                     uint4 i1 = *reinterpret_cast<const uint4 *>(w1i + cc + 8 * q);
+                    uint4 r0l = make_uint4(0, 0, 0, 0), i0l = r0l, r1l = r0l, i1l = r0l;
+                    if (passes == 3) {
+                        r0l = *reinterpret_cast<const uint4 *>(w0r + lo_off + cc + 8 * q);
+                        i0l = *reinterpret_cast<const uint4 *>(w0i + lo_off + cc + 8 * q);
+                        r1l = *reinterpret_cast<const uint4 *>(w1r + lo_off + cc + 8 * q);
+                        i1l = *reinterpret_cast<const uint4 *>(w1i + lo_off + cc + 8 * q);
+                    }
                     const __nv_bfloat162 *R0 = reinterpret_cast<const __nv_bfloat162 *>(&r0);
                     const __nv_bfloat162 *I0 = reinterpret_cast<const __nv_bfloat162 *>(&i0);
                     const __nv_bfloat162 *R1 = reinterpret_cast<const __nv_bfloat162 *>(&r1);
                     const __nv_bfloat162 *I1 = reinterpret_cast<const __nv_bfloat162 *>(&i1);
+                    const __nv_bfloat162 *R0l = reinterpret_cast<const __nv_bfloat162 *>(&r0l);
+                    const __nv_bfloat162 *I0l = reinterpret_cast<const __nv_bfloat162 *>(&i0l);
+                    const __nv_bfloat162 *R1l = reinterpret_cast<const __nv_bfloat162 *>(&r1l);
+                    const __nv_bfloat162 *I1l = reinterpret_cast<const __nv_bfloat162 *>(&i1l);
 #pragma unroll
                     for (int h = 0; h < 4; h++) {
                         float2 wr0 = __bfloat1622float2(R0[h]), wi0 = __bfloat1622float2(I0[h]);
                         float2 wr1 = __bfloat1622float2(R1[h]), wi1 = __bfloat1622float2(I1[h]);
+                        float2 t;
+                        t = __bfloat1622float2(R0l[h]); wr0.x += t.x; wr0.y += t.y;
+                        t = __bfloat1622float2(I0l[h]); wi0.x += t.x; wi0.y += t.y;
+                        t = __bfloat1622float2(R1l[h]); wr1.x += t.x; wr1.y += t.y;
+                        t = __bfloat1622float2(I1l[h]); wi1.x += t.x; wi1.y += t.y;
                         int j = 8 * q + 2 * h;
                         gre += wr0.x * a0r[j] - wi0.x * a0i[j] + sgn * (wr1.x * a1r[j] - wi1.x * a1i[j]);
                         gim += wr0.x * a0i[j] + wi0.x * a0r[j] + sgn * (wr1.x * a1i[j] + wi1.x * a1r[j]);
@@ -293,9 +328,19 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(
 
 // ---------------------------------------------------------------- operand synthesis
 
-// planes [4][Npad][Xpad]: Gre, Gim, (G v)re, (G v)im ; G_e[x] = C a exp(i 2 pi (f T - K/4 + 1/8))
+// value = hi + lo with hi = bf16(value), lo = bf16(value - hi) (split BF16)
+__device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, float v)
+{
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    *hi = h;
+    if (lo) *lo = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// planes [4][Npad][Xpad]: Gre, Gim, (G v)re, (G v)im (then 4 lo planes when split);
+// G_e[x] = C a exp(i 2 pi (f T - K/4 + 1/8))
 __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float *__restrict__ v, int N, int X, int Xpad,
-                               size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes)
+                               size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes,
+                               int split)
 {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= (size_t)N * X) return;
@@ -310,16 +355,18 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float *__
     }
     float vv = v[x];
     size_t o = (size_t)e * Xpad + x;
-    planes[o] = __float2bfloat16_rn(gr);
-    planes[pstride + o] = __float2bfloat16_rn(gi);
-    planes[2 * pstride + o] = __float2bfloat16_rn(gr * vv);
-    planes[3 * pstride + o] = __float2bfloat16_rn(gi * vv);
+    __nv_bfloat16 *lo = split ? planes + 4 * pstride : nullptr;
+    put_split(planes + o, lo ? lo + o : nullptr, gr);
+    put_split(planes + pstride + o, lo ? lo + pstride + o : nullptr, gi);
+    put_split(planes + 2 * pstride + o, lo ? lo + 2 * pstride + o : nullptr, gr * vv);
+    put_split(planes + 3 * pstride + o, lo ? lo + 3 * pstride + o : nullptr, gi * vv);
 }
 
 // planes [6][Xp][Npad] at [x][e]: u, conj(kappa) u, kappa u (re, im each);
 // u_e[x] = dgamma / (C a) exp(-i 2 pi (f T - K/4 + 1/8)), kappa = exp(i gamma)
 __global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, const float *__restrict__ dg, int N, int X, int Npad,
-                              size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes)
+                              size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes,
+                              int split)
 {
     __shared__ float sv[6][32][33];
     const int x0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
@@ -350,21 +397,23 @@ __global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, const float *__r
         if (x < X && e < N) {
             size_t o = (size_t)x * Npad + e;
 #pragma unroll
-            for (int k = 0; k < 6; k++) planes[k * pstride + o] = __float2bfloat16_rn(sv[k][tx][q]);
+            for (int k = 0; k < 6; k++)
+                put_split(planes + k * pstride + o, split ? planes + (6 + k) * pstride + o : nullptr, sv[k][tx][q]);
         }
     }
 }
 
-// R_s (complex N x N) -> planes [2][Npad][Npad]
-__global__ void k_rs_planes(const float2 *__restrict__ Rs, int N, int Npad, __nv_bfloat16 *__restrict__ planes)
+// R_s (complex N x N) -> planes [2][Npad][Npad] (then 2 lo planes when split)
+__global__ void k_rs_planes(const float2 *__restrict__ Rs, int N, int Npad, __nv_bfloat16 *__restrict__ planes,
+                            int split)
 {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= (size_t)N * N) return;
     int e = (int)(i / N), r = (int)(i % N);
     float2 v = Rs[i];
-    size_t o = (size_t)e * Npad + r;
-    planes[o] = __float2bfloat16_rn(v.x);
-    planes[(size_t)Npad * Npad + o] = __float2bfloat16_rn(v.y);
+    size_t o = (size_t)e * Npad + r, P = (size_t)Npad * Npad;
+    put_split(planes + o, split ? planes + 2 * P + o : nullptr, v.x);
+    put_split(planes + P + o, split ? planes + 3 * P + o : nullptr, v.y);
 }
 
 // gpart[0][x] = sum over emitter tiles (fixed order); gpart[1][x] = 0 (the stacks are
@@ -422,8 +471,10 @@ bool make_map(CUtensorMap *m, const void *base, size_t rows, size_t cols)
 
 // ---------------------------------------------------------------- API used by rbx_api.cu
 
-bool tc_setup(TcPlanes &p, int N, int X)
+bool tc_setup(TcPlanes &p, int N, int X, bool split)
 {
+    p.split = split;
+    const int mult = split ? 2 : 1;
     p.N = N;
     p.X = X;
     p.Npad = (N + BM - 1) / BM * BM;
@@ -442,22 +493,34 @@ bool tc_setup(TcPlanes &p, int N, int X)
     int kper = (nk + splits - 1) / splits;
     p.fwd_kper = kper;
     p.fwd_splits = (nk + kper - 1) / kper;
-    if (cudaMalloc(&p.fplanes, 4 * p.fwd_pstride * sizeof(__nv_bfloat16)) != cudaSuccess) return false;
-    if (cudaMalloc(&p.bplanes, 6 * p.bp_pstride * sizeof(__nv_bfloat16)) != cudaSuccess) return false;
-    if (cudaMalloc(&p.rsplanes, 2 * (size_t)p.Npad * p.Npad * sizeof(__nv_bfloat16)) != cudaSuccess) return false;
+    const size_t fbytes = mult * 4 * p.fwd_pstride * sizeof(__nv_bfloat16);
+    const size_t bbytes = mult * 6 * p.bp_pstride * sizeof(__nv_bfloat16);
+    const size_t rbytes = mult * 2 * (size_t)p.Npad * p.Npad * sizeof(__nv_bfloat16);
+    if (cudaMalloc(&p.fplanes, fbytes) != cudaSuccess) return false;
+    if (cudaMalloc(&p.bplanes, bbytes) != cudaSuccess) return false;
+    if (cudaMalloc(&p.rsplanes, rbytes) != cudaSuccess) return false;
     if (cudaMalloc(&p.bpart, (size_t)(p.Npad / BN) * p.Xp * sizeof(float2)) != cudaSuccess) return false;
     if (cudaMalloc(&p.err, sizeof(unsigned)) != cudaSuccess) return false;
-    cudaMemset(p.fplanes, 0, 4 * p.fwd_pstride * sizeof(__nv_bfloat16));
-    cudaMemset(p.bplanes, 0, 6 * p.bp_pstride * sizeof(__nv_bfloat16));
-    cudaMemset(p.rsplanes, 0, 2 * (size_t)p.Npad * p.Npad * sizeof(__nv_bfloat16));
+    cudaMemset(p.fplanes, 0, fbytes);
+    cudaMemset(p.bplanes, 0, bbytes);
+    cudaMemset(p.rsplanes, 0, rbytes);
     cudaMemset(p.err, 0, sizeof(unsigned));
     const __nv_bfloat16 *f = static_cast<const __nv_bfloat16 *>(p.fplanes);
     const __nv_bfloat16 *b = static_cast<const __nv_bfloat16 *>(p.bplanes);
     const __nv_bfloat16 *r = static_cast<const __nv_bfloat16 *>(p.rsplanes);
+    const size_t P = (size_t)p.Npad * p.Npad;
     bool ok = true;
-    for (int k = 0; k < 4; k++) ok = ok && make_map(&p.fmaps[k], f + k * p.fwd_pstride, p.Npad, p.Xpad);
-    for (int k = 0; k < 4; k++) ok = ok && make_map(&p.bmaps[k], b + k * p.bp_pstride, p.Xp, p.Npad);
-    for (int k = 0; k < 2; k++) ok = ok && make_map(&p.bmaps[4 + k], r + (size_t)k * p.Npad * p.Npad, p.Npad, p.Npad);
+    for (int h = 0; h < mult; h++) {
+        const __nv_bfloat16 *fh = f + (size_t)h * 4 * p.fwd_pstride, *bh = b + (size_t)h * 6 * p.bp_pstride,
+                            *rh = r + (size_t)h * 2 * P;
+        for (int k = 0; k < 4; k++) ok = ok && make_map(&p.fmaps[h][k], fh + k * p.fwd_pstride, p.Npad, p.Xpad);
+        for (int k = 0; k < 4; k++) ok = ok && make_map(&p.bmaps[h][k], bh + k * p.bp_pstride, p.Xp, p.Npad);
+        for (int k = 0; k < 2; k++) ok = ok && make_map(&p.bmaps[h][4 + k], rh + (size_t)k * P, p.Npad, p.Npad);
+    }
+    if (!split) {
+        for (int k = 0; k < 4; k++) p.fmaps[1][k] = p.fmaps[0][k];
+        for (int k = 0; k < 6; k++) p.bmaps[1][k] = p.bmaps[0][k];
+    }
     if (!ok) return false;
     ok = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM) == cudaSuccess &&
          cudaFuncSetAttribute(k_backproject_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM) ==
@@ -486,10 +549,12 @@ int launch_forward_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     k_synth_fwd_tc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, v, p.N, p.X, p.Xpad, p.fwd_pstride, fhi, flo,
                                                                green_const_tc(f, c0),
-                                                               static_cast<__nv_bfloat16 *>(p.fplanes));
+                                                               static_cast<__nv_bfloat16 *>(p.fplanes), p.split);
     int T = p.Npad / BM, pairs = T * (T + 1) / 2;
-    k_forward_tc<<<dim3(pairs, p.fwd_splits), 192, F_SMEM, s>>>(p.fmaps[0], p.fmaps[1], p.fmaps[2], p.fmaps[3], p.N, T,
-                                                                p.Xpad / BK, p.fwd_kper, part, p.err);
+    Maps4 hi{p.fmaps[0][0], p.fmaps[0][1], p.fmaps[0][2], p.fmaps[0][3]};
+    Maps4 lo{p.fmaps[1][0], p.fmaps[1][1], p.fmaps[1][2], p.fmaps[1][3]};
+    k_forward_tc<<<dim3(pairs, p.fwd_splits), 192, F_SMEM, s>>>(hi, lo, p.split ? 3 : 1, p.N, T, p.Xpad / BK,
+                                                                p.fwd_kper, part, p.err);
     return p.fwd_splits;
 }
 
@@ -498,18 +563,20 @@ void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, doubl
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
     k_synth_bp_tc<<<grd, 256, 0, s>>>(tab, dg, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
-                                      static_cast<__nv_bfloat16 *>(p.bplanes));
+                                      static_cast<__nv_bfloat16 *>(p.bplanes), p.split);
 }
 
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s)
 {
     size_t nn = (size_t)p.N * p.N;
     k_rs_planes<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(Rs, p.N, p.Npad,
-                                                             static_cast<__nv_bfloat16 *>(p.rsplanes));
+                                                             static_cast<__nv_bfloat16 *>(p.rsplanes), p.split);
     dim3 grd(p.Npad / BN, p.Xp / BM);
-    k_backproject_tc<<<grd, 192, B_SMEM, s>>>(p.bmaps[0], p.bmaps[1], p.bmaps[2], p.bmaps[3], p.bmaps[4], p.bmaps[5],
-                                              static_cast<const __nv_bfloat16 *>(p.bplanes), p.bp_pstride, p.Npad,
-                                              p.Npad / BK, weight_mode == 0 ? -1.f : 1.f, p.bpart, p.Xp, p.err);
+    Maps6 hi{p.bmaps[0][0], p.bmaps[0][1], p.bmaps[0][2], p.bmaps[0][3], p.bmaps[0][4], p.bmaps[0][5]};
+    Maps6 lo{p.bmaps[1][0], p.bmaps[1][1], p.bmaps[1][2], p.bmaps[1][3], p.bmaps[1][4], p.bmaps[1][5]};
+    k_backproject_tc<<<grd, 192, B_SMEM, s>>>(hi, lo, p.split ? 3 : 1, static_cast<const __nv_bfloat16 *>(p.bplanes),
+                                              p.bp_pstride, p.Npad, p.Npad / BK, weight_mode == 0 ? -1.f : 1.f,
+                                              p.bpart, p.Xp, p.err);
     k_bp_reduce<<<(p.X + 255) / 256, 256, 0, s>>>(p.bpart, p.Npad / BN, p.Xp, p.X, gpart);
 }
 

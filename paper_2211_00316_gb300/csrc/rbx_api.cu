@@ -152,8 +152,8 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     NEED(j, std::isfinite(g.ds) && g.ds > 0, RBX_EINVAL, "ds must be > 0");
     NEED(j, g.weight_mode == 0 || g.weight_mode == 1, RBX_EINVAL, "weight_mode must be 0 or 1");
     NEED(j, std::isfinite(g.tau), RBX_EINVAL, "tau must be finite");
-    NEED(j, g.precision == RBX_FP32 || g.precision == RBX_BF16, RBX_EINVAL,
-         "precision must be RBX_FP32 or RBX_BF16 (split BF16 is not available yet)");
+    NEED(j, g.precision >= RBX_FP32 && g.precision <= RBX_BF16X3, RBX_EINVAL,
+         "precision must be RBX_FP32, RBX_BF16 or RBX_BF16X3");
     double xl = g.x0, xr = g.x0 + (g.nx - 1) * g.dx, yl = g.y0, yr = g.y0 + (g.ny - 1) * g.dx;
     NEED(j, xl <= -g.ring_radius - g.dx && xr >= g.ring_radius + g.dx && yl <= -g.ring_radius - g.dx &&
                 yr >= g.ring_radius + g.dx,
@@ -208,7 +208,7 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     ALLOC(w.Rs, N * N);
     ALLOC(w.data, N * N);
     if (g.precision != RBX_FP32) {
-        if (!tc_setup(w.tc, w.N, X)) {
+        if (!tc_setup(w.tc, w.N, X, g.precision == RBX_BF16X3)) {
             cudaGetLastError();
             free_ws(w);
             return fail(j, RBX_ENOMEM, "tensor-core operand set-up failed (allocation or TMA descriptor)");
@@ -359,7 +359,7 @@ static rbx_status forward_core(rbx_job *j, double f, bool timed)
 {
     Workspace &w = j->w;
     rbx_status st;
-    if (j->g.precision == RBX_BF16) {
+    if (j->g.precision != RBX_FP32) {
         // the BF16 operand synthesis is fused into the first launch of launch_forward_tc
         if (timed && (st = record(j, EV_SYNTH_F))) return st;
         int splits = launch_forward_tc(w.tc, w.tab, w.v, f, j->g.c0, w.part, j->stream);
@@ -416,7 +416,7 @@ rbx_status rbx_adjoint(rbx_job *j, double f, const void *R_dev, void *out_dev, i
     Workspace &w = j->w;
     launch_symmetrize(static_cast<const float2 *>(R_dev), w.N, w.Rs, j->stream);
     LAUNCHED(j, 1);
-    if (preconditioned && j->g.precision == RBX_BF16) {
+    if (preconditioned && j->g.precision != RBX_FP32) {
         launch_synth_bp_tc(w.tc, w.tab, w.dg, f, j->g.c0, j->stream);
         launch_backproject_tc(w.tc, w.Rs, j->g.weight_mode, w.gpart, j->stream);
         launch_combine_adjoint(w.gpart, w.X, 0, j->g.weight_mode, 2.0, static_cast<float2 *>(out_dev), j->stream);
@@ -454,7 +454,7 @@ static rbx_status update_core(rbx_job *j, double f, double df, const float2 *dat
     double r2 = 0;
     CUDA_TRY(j, cudaMemcpyAsync(&r2, w.red + residual_blocks(w.N), sizeof r2, cudaMemcpyDeviceToHost, j->stream));
     if ((st = record(j, EV_RESID))) return st;
-    if (j->g.precision == RBX_BF16) {
+    if (j->g.precision != RBX_FP32) {
         launch_synth_bp_tc(w.tc, w.tab, w.dg, f, j->g.c0, j->stream);
         LAUNCHED(j, 1);
         if ((st = record(j, EV_SYNTH_B))) return st;

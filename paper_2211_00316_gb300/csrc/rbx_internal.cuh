@@ -35,12 +35,13 @@ struct TcPlanes {
     int N = 0, X = 0, Npad = 0, Xpad = 0, Xp = 0, sms = 0;
     size_t fwd_pstride = 0, bp_pstride = 0;
     int fwd_splits = 1, fwd_kper = 1;
+    bool split = false;        // split BF16: every plane set is followed by its lo set
     void *fplanes = nullptr;   // [4][Npad][Xpad] bf16: Gre, Gim, (Gv)re, (Gv)im
     void *bplanes = nullptr;   // [6][Xp][Npad] bf16: u, conj(kappa) u, kappa u (re, im)
     void *rsplanes = nullptr;  // [2][Npad][Npad] bf16: R_s re, im
     float2 *bpart = nullptr;   // [Npad/128][Xp] partial back-projection
     unsigned *err = nullptr;   // bounded-wait timeouts of the tensor-core kernels
-    CUtensorMap fmaps[4], bmaps[6];
+    CUtensorMap fmaps[2][4], bmaps[2][6];   // [hi, lo]
     bool ready = false;
 };
 
@@ -99,7 +100,7 @@ void launch_backproject_simt(const float2 *A, const float2 *kap, const float2 *R
                              float2 *gpart, cudaStream_t s);
 
 // k_gemm_tc.cu (BF16 tensor cores)
-bool tc_setup(TcPlanes &p, int N, int X);
+bool tc_setup(TcPlanes &p, int N, int X, bool split);
 void tc_free(TcPlanes &p);
 int launch_forward_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, float2 *part,
                       cudaStream_t s);
