@@ -56,8 +56,14 @@ struct Maps4 {
     CUtensorMap are, aim, bre, bim;
 };
 
-// passes = 1: A_hi B_hi. passes = 3 (split BF16): A_hi B_hi + A_hi B_lo + A_lo B_hi, all
-// accumulated into the same tensor-memory accumulators.
+// passes = 1: A_hi B_hi. passes = 3 (split BF16): A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// With split BF16 the tensor-memory accumulators are drained every kSeg K chunks into the
+// CTA's FP32 partial tile in global memory (the CTA owns that tile), so no accumulation in
+// tensor memory runs over more than kSeg x 64 mask nodes (its long-K rounding would
+// otherwise exceed the split's own error); two accumulator buffers alternate so the MMAs
+// never wait for the drain. Plain BF16, whose error is its input rounding, uses one segment.
+constexpr int kSeg = 16;
+
 __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ Maps4 hi, const __grid_constant__ Maps4 lo,
                                                        int passes, int N, int ntile, int nk, int kper,
                                                        float2 *__restrict__ part, unsigned *__restrict__ err)
@@ -66,8 +72,9 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ M
     uint8_t *tiles = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)F_STAGES * F_TILES * TILE);
     uint64_t *empty = full + F_STAGES;
-    uint64_t *accb = empty + F_STAGES;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    uint64_t *accf = empty + F_STAGES;     // [2] accumulator buffer ready to drain
+    uint64_t *acce = accf + 2;             // [2] accumulator buffer drained
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     int b = blockIdx.x, te = 0;
@@ -76,13 +83,15 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ M
     const int split = blockIdx.y;
     const int c0 = split * kper, nc = min(nk, c0 + kper) - c0;
     const int ntot = passes * nc;
+    const int seglen = passes == 3 ? kSeg : (ntot > 0 ? ntot : 1);
+    const int nseg = (ntot + seglen - 1) / seglen;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < F_STAGES; s++) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
-        mbar_init(accb, 1);
+        for (int q = 0; q < 2; q++) { mbar_init(accf + q, 1); mbar_init(acce + q, 128); }
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(tslot, 256);
+    if (warp == 1) tmem_alloc(tslot, 512);
     fence_before();
     __syncthreads();
     fence_after();
@@ -111,58 +120,79 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ M
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t ip = idesc_bf16(BM, BN, 0), in = idesc_bf16(BM, BN, 1);
-            const uint32_t dre = tmem, dim = tmem + BN;
-            for (int c = 0; c < ntot; c++) {
+            bool ok = true;
+            for (int c = 0; c < ntot && ok; c++) {
+                const int seg = c / seglen, cs = c - seg * seglen, buf = seg & 1;
+                if (cs == 0 && seg >= 2) {
+                    if (!mbar_wait(acce + buf, ((seg >> 1) - 1) & 1)) { atomicOr(err, 32u); ok = false; break; }
+                    fence_after();
+                }
+                const uint32_t dre = tmem + buf * 2 * BN, dim = dre + BN;
                 int s = c % F_STAGES;
-                if (!mbar_wait(full + s, (c / F_STAGES) & 1)) { atomicOr(err, 2u); break; }
+                if (!mbar_wait(full + s, (c / F_STAGES) & 1)) { atomicOr(err, 2u); ok = false; break; }
                 fence_after();
                 uint32_t base = smem_u32(tiles + (size_t)s * F_TILES * TILE);
 #pragma unroll
                 for (int k = 0; k < BK / 16; k++) {
                     uint64_t a0 = desc_sw128(base + k * 32), a1 = desc_sw128(base + TILE + k * 32);
                     uint64_t b0 = desc_sw128(base + 2 * TILE + k * 32), b1 = desc_sw128(base + 3 * TILE + k * 32);
-                    uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                    uint32_t acc = (cs > 0 || k > 0) ? 1u : 0u;
                     mma_bf16(dre, a0, b0, ip, acc);
                     mma_bf16(dre, a1, b1, in, 1u);
                     mma_bf16(dim, a0, b1, ip, acc);
                     mma_bf16(dim, a1, b0, ip, 1u);
                 }
                 mma_commit(empty + s);
+                if (cs == seglen - 1 || c == ntot - 1) mma_commit(accf + buf);
             }
-            mma_commit(accb);
-            if (!mbar_wait(accb, 0)) atomicOr(err, 8u);
+            // every MMA of this CTA has completed once the last buffer is signalled
+            if (ntot > 0 && !mbar_wait(accf + ((nseg - 1) & 1), ((nseg - 1) >> 1) & 1)) atomicOr(err, 8u);
         }
         __syncwarp();
     } else if (warp >= 2) {
         const int sub = warp & 3, row = sub * 32 + lane;
-        bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0));
-        fence_after();
-        if (ok) {
-            const int e = te * BM + row;
-            float2 *P = part + (size_t)split * N * N + (size_t)e * N;
-            const uint32_t lanes = (uint32_t)(sub * 32) << 16;
+        const int e = te * BM + row;
+        float2 *P = part + (size_t)split * N * N + (size_t)e * N;
+        const uint32_t lanes = (uint32_t)(sub * 32) << 16;
+        for (int sg = 0; sg < nseg; sg++) {
+            const int buf = sg & 1;
+            bool ok = __all_sync(0xffffffffu, mbar_wait(accf + buf, (sg >> 1) & 1));
+            fence_after();
+            if (!ok) {
+                if (lane == 0) atomicOr(err, 16u);
+                break;
+            }
+            const uint32_t dre = tmem + buf * 2 * BN;
 #pragma unroll 1
             for (int cc = 0; cc < BN; cc += 32) {
                 float vr[32], vi[32];
-                tmem_ld32(tmem + lanes + cc, vr);
-                tmem_ld32(tmem + lanes + BN + cc, vi);
+                tmem_ld32(tmem + lanes + (dre - tmem) + cc, vr);
+                tmem_ld32(tmem + lanes + (dre - tmem) + BN + cc, vi);
                 if (e < N) {
 #pragma unroll
                     for (int i = 0; i < 32; i++) {
                         int r = tr * BN + cc + i;
-                        if (r < N) P[r] = make_float2(vr[i], vi[i]);
+                        if (r < N) {
+                            float2 v = make_float2(vr[i], vi[i]);
+                            if (sg > 0) {
+                                float2 o = P[r];
+                                v.x += o.x;
+                                v.y += o.y;
+                            }
+                            P[r] = v;
+                        }
                     }
                 }
             }
-        } else if (lane == 0) {
-            atomicOr(err, 16u);
+            fence_before();
+            mbar_arrive(acce + buf);
         }
     }
     fence_before();
     __syncthreads();
     if (warp == 1) {
         fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, 512);
     }
 }
 

@@ -28,6 +28,14 @@ struct Fv {
     float n, gx, gy, hxx, hxy, hyy;
 };
 
+// s += inc with compensation term c (Kahan): the ray state is a sum of ~10^3 small steps
+__device__ __forceinline__ void kadd(float &s, float &c, float inc)
+{
+    const float y = inc - c, t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 __device__ __forceinline__ void field_eval(const float *__restrict__ F, const RayParams &p, float px, float py, Fv &o)
 {
     float u = (px - p.x0) * p.inv_dx, v = (py - p.y0) * p.inv_dx;
@@ -284,6 +292,8 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
     Fv F1;
     field_eval(F, p, x, y, F1);
     float px, py, dpx, dpy, dxx = 0.f, dxy = 0.f, T = 0.f, Tc = 0.f;
+    // compensation terms of x, p, dx (T has Tc)
+    float cx = 0.f, cy = 0.f, cpx = 0.f, cpy = 0.f, cdx = 0.f, cdy = 0.f;
     {
         float s0, c0;
         sincosf(gam0, &s0, &c0);
@@ -303,6 +313,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             const float n = F1.n, in = 1.f / n;
             const float sc = n * rsqrtf(px * px + py * py);
             px *= sc; py *= sc;
+            cpx *= sc; cpy *= sc;
             const float qx = px * in, qy = py * in;
             // stage 2 at the auxiliary point x + ds q_x
             Fv F2;
@@ -314,8 +325,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             const float qax = pax * ina, qay = pay * ina;
             const float sx = qx + qax, sy = qy + qay, rs = rsqrtf(sx * sx + sy * sy);
             const float dirx = sx * rs, diry = sy * rs;
-            float xn = x + ds * dirx, yn = y + ds * diry;
-            float pxn = px + hds * (F1.gx + F2.gx), pyn = py + hds * (F1.gy + F2.gy);
+            const float ddpx = hds * (F1.gx + F2.gx), ddpy = hds * (F1.gy + F2.gy);
             // paraxial system, both stages at the reference ray's stage values:
             // q_dx = (dp - p (g.dx)/n)/n, q_dp = H dx + g ((p.dp)/n - g.dx)/n
             const float gd = F1.gx * dxx + F1.gy * dxy, pd = px * dpx + py * dpy;
@@ -330,8 +340,9 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             const float w2 = ina * (pda * ina - gda);
             const float qdpax = F2.hxx * dxax + F2.hxy * dxay + F2.gx * w2;
             const float qdpay = F2.hxy * dxax + F2.hyy * dxay + F2.gy * w2;
-            float dxxn = dxx + hds * (qdxx + qdxax), dxyn = dxy + hds * (qdxy + qdxay);
-            float dpxn = dpx + hds * (qdpx + qdpax), dpyn = dpy + hds * (qdpy + qdpay);
+            const float ddxx = hds * (qdxx + qdxax), ddxy = hds * (qdxy + qdxay);
+            const float ddpx2 = hds * (qdpx + qdpax), ddpy2 = hds * (qdpy + qdpay);
+            const float xn = x + ds * dirx, yn = y + ds * diry;
             field_eval(F, p, xn, yn, F2);                // fields at the new sample (reused next step)
             float inc = hds * (n + F2.n);
             const bool last = xn * xn + yn * yn >= R2;
@@ -343,19 +354,19 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
                 float t = -b + sqrtf(disc > 0.f ? disc : 0.f);
                 t = fminf(fmaxf(t, 0.f), ds);
                 float fr = t / ds;
-                xn = x + t * dirx; yn = y + t * diry;
+                x = x + t * dirx; y = y + t * diry;
                 inc *= fr;
-                dxxn = dxx + fr * (dxxn - dxx); dxyn = dxy + fr * (dxyn - dxy);
-                dpxn = dpx + fr * (dpxn - dpx); dpyn = dpy + fr * (dpyn - dpy);
-                pxn = px + fr * (pxn - px); pyn = py + fr * (pyn - py);
-                field_eval(F, p, xn, yn, F2);
+                dxx += fr * ddxx; dxy += fr * ddxy;
+                dpx += fr * ddpx2; dpy += fr * ddpy2;
+                px += fr * ddpx; py += fr * ddpy;
+                field_eval(F, p, x, y, F2);
+            } else {
+                kadd(x, cx, ds * dirx); kadd(y, cy, ds * diry);
+                kadd(px, cpx, ddpx); kadd(py, cpy, ddpy);
+                kadd(dxx, cdx, ddxx); kadd(dxy, cdy, ddxy);
+                dpx += ddpx2; dpy += ddpy2;
             }
-            {   // compensated travel-time sum (trapezoid of n along the samples)
-                float yk = inc - Tc, tk = T + yk;
-                Tc = (tk - T) - yk;
-                T = tk;
-            }
-            x = xn; y = yn; px = pxn; py = pyn; dxx = dxxn; dxy = dxyn; dpx = dpxn; dpy = dpyn;
+            kadd(T, Tc, inc);   // trapezoid of n along the samples
             F1 = F2;
             const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
             const float J = dxx * ty - dxy * tx;
