@@ -223,9 +223,9 @@ def main():
 
     import torch
     import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2211_00316_gb300 import replicas as REP
+    info = REP.RankInfo.from_env()
+    world, rank, local = info.world, info.rank, info.local
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -240,7 +240,7 @@ def main():
     from paper_2211_00316_gb300 import rbx
 
     prec = {"fp32": rbx.RBX_FP32, "bf16": rbx.RBX_BF16, "bf16x3": rbx.RBX_BF16X3}[args.precision]
-    w = workload(args.workload, rank)
+    w = workload(args.workload, REP.replica_seed(rank))
     g = w.geom
     stream = torch.cuda.Stream()
     total_steps = args.warmup + args.steps
@@ -279,12 +279,10 @@ def main():
         torch.cuda.synchronize()
         clk = clocks.stop()
         ms = ev0.elapsed_time(ev1)
+        ms = REP.max_over_ranks(ms, "cuda")
         if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
-        value = world * args.steps / (ms / 1e3)
+        value = REP.aggregate_throughput(world * args.steps, ms / 1e3)
 
         # end to end through the host-buffer entry point: H2D of the step's data and D2H of the model
         e2e = None
@@ -300,12 +298,9 @@ def main():
             for k in range(args.warmup, total_steps):
                 job.update_frequency_host(float(w.freqs[fidx[k]]), df, data_host[fidx[k]], c_host)
             torch.cuda.synchronize()
-            el = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([el], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                el = float(t.item())
-            e2e = {"value": world * args.steps / el, "unit": UNIT, "h2d_bytes_per_step": N * N * 8,
+            el = REP.max_over_ranks(time.perf_counter() - t0, "cuda")
+            e2e = {"value": REP.aggregate_throughput(world * args.steps, el), "unit": UNIT,
+                   "h2d_bytes_per_step": N * N * 8,
                    "d2h_bytes_per_step": g.nx * g.ny * 4}
         job.close()
 
