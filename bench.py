@@ -41,6 +41,8 @@ def workload(name: str, seed: int):
         w = P.breast(1024, 512, 0.45e-3, 110e-3, np.linspace(1e5, 1.2e6, 20), seed=seed, name="ring1024_grid512_breast")
     elif name == "fp32_ring256":
         w = P.breast(256, 288, 0.8e-3, 110e-3, np.linspace(1e5, 1e6, 10), seed=seed, name="ring256_grid288_breast")
+    elif name == "ring1024_grid288":
+        w = P.breast(1024, 288, 0.8e-3, 110e-3, np.linspace(1e5, 1e6, 10), seed=seed, name="ring1024_grid288_breast")
     elif name == "small":
         w = P.small_two_disc()
     else:
@@ -78,7 +80,10 @@ def kernel_src_hash() -> str:
 
 # DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (workload, kernel); valid only for the kernel sources they were taken on.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_trace_raster -s 2 -c 1 (1 pass)
+    ("precision_ring1024", "trace"): {"bytes": 2.52e9 + 2.48e9, "src": "c14d9d3759c8"},
+}
 
 
 def algorithmic(kernel: str, N: int, X: int, precision: str):
@@ -213,7 +218,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rbx", choices=["rbx", "reference"])
-    ap.add_argument("--workload", default="precision_ring1024", choices=["precision_ring1024", "fp32_ring256", "small"])
+    ap.add_argument("--workload", default="precision_ring1024", choices=["precision_ring1024", "fp32_ring256", "ring1024_grid288", "small"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
