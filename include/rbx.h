@@ -167,6 +167,26 @@ rbx_status rbx_update_from_tables(rbx_job *job, double freq_hz, double dfreq_hz,
 rbx_status rbx_update_frequency_host(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_host,
                                      float *c_out_host, rbx_stats *out);
 
+/* Queue one update exactly as rbx_update_frequency does, without waiting for it: nothing is
+ * copied to the host, so the call can be captured into a CUDA graph. Its scalar results go to
+ * device stats slot `slot` (0..63) of the job; read them with rbx_get_stats. */
+rbx_status rbx_update_frequency_async(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_dev, int slot);
+
+/* Wait for the job's stream and return the scalar results kept in stats slot `slot`
+ * (timings are not filled). Returns the status the update in that slot ended with
+ * (RBX_ENUMERIC, RBX_ETIMEOUT, ...). */
+rbx_status rbx_get_stats(rbx_job *job, int slot, rbx_stats *out);
+
+/* Batched form: the full low-to-high sweeps of n independent jobs (slices of different
+ * sizes), freqs[i][0..nf[i]-1] with data_dev[i] holding nf[i] N_i x N_i blocks, nf[i] <= 64.
+ * Each job's sweep runs on a stream of its own, forked from and joined to one origin stream;
+ * with use_graph != 0 the whole fork/join is captured into one CUDA graph and launched once,
+ * otherwise it is queued directly. Results are the same as running the jobs one after the
+ * other. last[i] (nullable) receives job i's last update's scalars; ms_total (nullable) the
+ * device time of the whole batch. The jobs' own streams are drained first and kept. */
+rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs, const int *nf,
+                         const void *const *data_dev, int use_graph, rbx_stats *last, float *ms_total);
+
 /* Low-to-high frequency sweep (Sec. 3.4): one update per frequency freqs_hz[0..nf-1]
  * (host array), data_dev holding nf consecutive N x N complex64 blocks; df of frequency n
  * is half the distance between its neighbours (one-sided at the ends; 1 MHz / 10 when

@@ -65,7 +65,7 @@ static cudaError_t dalloc(T *&p, size_t n)
 
 static void free_ws(Workspace &w)
 {
-    void *ps[] = {w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
+    void *ps[] = {w.hist, w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
                   w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -199,8 +199,10 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     ALLOC(w.dg, NX);
     ALLOC(w.exits, N * (N - 1));
     ALLOC(w.G, NX);
-    ALLOC(w.U, NX);
-    ALLOC(w.kap, NX);
+    if (g.precision == RBX_FP32) {   // FP32 back-projection operands (the tensor-core path has its own)
+        ALLOC(w.U, NX);
+        ALLOC(w.kap, NX);
+    }
     ALLOC(w.v, X);
     ALLOC(w.gdir, N * N);
     ALLOC(w.D, N * N);
@@ -217,10 +219,10 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     }
     ALLOC(w.part, (size_t)w.fwd_splits * N * N);
     ALLOC(w.gpart, 2 * (size_t)X);
-    size_t nred = (size_t)residual_blocks(w.N) + 8;
-    size_t nred2 = 3 * (size_t)update_blocks(g.nx, g.ny) + 8;
-    ALLOC(w.red, nred > nred2 ? nred : nred2);
+    // residual partials + total, then the update's partials + totals (disjoint regions)
+    ALLOC(w.red, (size_t)residual_blocks(w.N) + 8 + 3 * (size_t)update_blocks(g.nx, g.ny) + 8);
     ALLOC(w.counters, 8);
+    ALLOC(w.hist, (size_t)kHistSlots * kHistStride);
 #undef ALLOC
     launch_mask_idx(w.node2x, (int)nxy, w.idx, j->stream);
     launch_mask_rows(w.node2x, g.nx, g.ny, w.rows, j->stream);
@@ -436,7 +438,9 @@ rbx_status rbx_adjoint(rbx_job *j, double f, const void *R_dev, void *out_dev, i
     return RBX_OK;
 }
 
-static rbx_status update_core(rbx_job *j, double f, double df, const float2 *data, rbx_stats *out, bool traced)
+// Steps a5-a9 queued on the job's stream with no host interaction (capturable into a CUDA
+// graph); the update's scalar results are copied into device history slot `slot`.
+static rbx_status enqueue_update(rbx_job *j, double f, double df, const float2 *data, bool traced, int slot)
 {
     Workspace &w = j->w;
     rbx_status st;
@@ -451,8 +455,6 @@ static rbx_status update_core(rbx_job *j, double f, double df, const float2 *dat
     if ((st = forward_core(j, f, true))) return st;
     launch_residual(w.gdir, w.D, data, w.N, nullptr, w.Rs, w.red, j->stream);
     LAUNCHED(j, 2);
-    double r2 = 0;
-    CUDA_TRY(j, cudaMemcpyAsync(&r2, w.red + residual_blocks(w.N), sizeof r2, cudaMemcpyDeviceToHost, j->stream));
     if ((st = record(j, EV_RESID))) return st;
     if (j->g.precision != RBX_FP32) {
         launch_synth_bp_tc(w.tc, w.tab, w.dg, f, j->g.c0, j->stream);
@@ -468,51 +470,64 @@ static rbx_status update_core(rbx_job *j, double f, double df, const float2 *dat
         LAUNCHED(j, 1);
     }
     if ((st = record(j, EV_GEMM_B))) return st;
-    launch_update(w.gpart, w.node2x, w.nx, w.ny, w.X, j->g.weight_mode, f, df, j->g.tau, j->g.c0, w.c, w.red,
+    const int roff = residual_blocks(w.N) + 8;
+    launch_update(w.gpart, w.node2x, w.nx, w.ny, w.X, j->g.weight_mode, f, df, j->g.tau, j->g.c0, w.c, w.red + roff,
                   w.counters, j->stream);
-    LAUNCHED(j, 2);
+    launch_snapshot(w.red + residual_blocks(w.N), w.red + roff + 3 * update_blocks(w.nx, w.ny), w.counters,
+                    w.tc.err, w.hist + (size_t)slot * kHistStride, j->stream);
+    LAUNCHED(j, 3);
     if ((st = record(j, EV_UPDATE))) return st;
     j->ns_valid = false;   // the model changed
-    int nb = update_blocks(w.nx, w.ny);
-    double tot[3];
-    unsigned long long cnt[8];
-    CUDA_TRY(j, cudaMemcpyAsync(tot, w.red + 3 * nb, sizeof tot, cudaMemcpyDeviceToHost, j->stream));
-    CUDA_TRY(j, cudaMemcpyAsync(cnt, w.counters, sizeof cnt, cudaMemcpyDeviceToHost, j->stream));
+    return RBX_OK;
+}
+
+// Scalar results of history slot `slot` as an rbx_stats (synchronises); returns the
+// status the update ended with.
+static rbx_status read_stats(rbx_job *j, int slot, rbx_stats *out, bool traced, bool timing)
+{
+    Workspace &w = j->w;
+    double h[kHistStride];
+    CUDA_TRY(j, cudaMemcpyAsync(h, w.hist + (size_t)slot * kHistStride, sizeof h, cudaMemcpyDeviceToHost, j->stream));
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     if (out) {
         std::memset(out, 0, sizeof *out);
-        out->resid_norm2 = r2;
-        out->rms_dc = std::sqrt(tot[0] / w.X);
-        out->max_abs_dc = tot[1];
-        out->dm_norm = std::sqrt(tot[2]);
-        out->n_uncovered = (long long)cnt[0];
-        out->n_clamped = (long long)cnt[1];
-        out->n_launches = j->launches;
-        int t0 = traced ? EV_START : EV_TABLES;
-        out->ms_trace = traced ? elapsed(j, EV_START, EV_TABLES) : 0.f;
-        out->ms_forward = elapsed(j, EV_TABLES, EV_RESID);
-        out->ms_backproj = elapsed(j, EV_RESID, EV_UPDATE);
-        out->ms_total = elapsed(j, t0, EV_UPDATE);
-        if (traced) {
-            out->ms_kernel[RBX_K_FIELDS] = elapsed(j, EV_START, EV_FIELDS);
-            out->ms_kernel[RBX_K_TRACE] = elapsed(j, EV_FIELDS, EV_TRACE);
+        out->resid_norm2 = h[0];
+        out->rms_dc = std::sqrt(h[1] / w.X);
+        out->max_abs_dc = h[2];
+        out->dm_norm = std::sqrt(h[3]);
+        out->n_uncovered = (long long)h[4];
+        out->n_clamped = (long long)h[5];
+        if (timing) {
+            int t0 = traced ? EV_START : EV_TABLES;
+            out->ms_trace = traced ? elapsed(j, EV_START, EV_TABLES) : 0.f;
+            out->ms_forward = elapsed(j, EV_TABLES, EV_RESID);
+            out->ms_backproj = elapsed(j, EV_RESID, EV_UPDATE);
+            out->ms_total = elapsed(j, t0, EV_UPDATE);
+            if (traced) {
+                out->ms_kernel[RBX_K_FIELDS] = elapsed(j, EV_START, EV_FIELDS);
+                out->ms_kernel[RBX_K_TRACE] = elapsed(j, EV_FIELDS, EV_TRACE);
+            }
+            out->ms_kernel[RBX_K_TABLES] =
+                (traced ? elapsed(j, EV_TRACE, EV_TABLES) : 0.f) + elapsed(j, EV_TABLES, EV_GDIR);
+            out->ms_kernel[RBX_K_SYNTH_FWD] = elapsed(j, EV_GDIR, EV_SYNTH_F);
+            out->ms_kernel[RBX_K_GEMM_FWD] = elapsed(j, EV_SYNTH_F, EV_GEMM_F);
+            out->ms_kernel[RBX_K_SYNTH_BP] = elapsed(j, EV_RESID, EV_SYNTH_B);
+            out->ms_kernel[RBX_K_GEMM_BP] = elapsed(j, EV_SYNTH_B, EV_GEMM_B);
+            out->ms_kernel[RBX_K_UPDATE] = elapsed(j, EV_GEMM_F, EV_RESID) + elapsed(j, EV_GEMM_B, EV_UPDATE);
         }
-        out->ms_kernel[RBX_K_TABLES] = (traced ? elapsed(j, EV_TRACE, EV_TABLES) : 0.f) + elapsed(j, EV_TABLES, EV_GDIR);
-        out->ms_kernel[RBX_K_SYNTH_FWD] = elapsed(j, EV_GDIR, EV_SYNTH_F);
-        out->ms_kernel[RBX_K_GEMM_FWD] = elapsed(j, EV_SYNTH_F, EV_GEMM_F);
-        out->ms_kernel[RBX_K_SYNTH_BP] = elapsed(j, EV_RESID, EV_SYNTH_B);
-        out->ms_kernel[RBX_K_GEMM_BP] = elapsed(j, EV_SYNTH_B, EV_GEMM_B);
-        out->ms_kernel[RBX_K_UPDATE] = elapsed(j, EV_GEMM_F, EV_RESID) + elapsed(j, EV_GEMM_B, EV_UPDATE);
     }
-    if (w.tc.err) {
-        unsigned terr = 0;
-        CUDA_TRY(j, cudaMemcpy(&terr, w.tc.err, sizeof terr, cudaMemcpyDeviceToHost));
-        NEED(j, terr == 0, RBX_ETIMEOUT, "a tensor-core kernel's bounded wait gave up");
-    }
-    NEED(j, cnt[4] == 0, RBX_ENUMERIC, "non-finite or non-positive updated squared slowness");
-    NEED(j, cnt[2] == 0, RBX_ENUMERIC, "a ray did not reach the ring within the step limit");
-    NEED(j, cnt[3] == 0, RBX_ECUDA, "table compare-and-swap exceeded its iteration bound");
+    NEED(j, h[10] == 0, RBX_ETIMEOUT, "a tensor-core kernel's bounded wait gave up");
+    NEED(j, h[8] == 0, RBX_ENUMERIC, "non-finite or non-positive updated squared slowness");
+    NEED(j, h[6] == 0, RBX_ENUMERIC, "a ray did not reach the ring within the step limit");
+    NEED(j, h[7] == 0, RBX_ECUDA, "table compare-and-swap exceeded its iteration bound");
     return RBX_OK;
+}
+
+static rbx_status update_core(rbx_job *j, double f, double df, const float2 *data, rbx_stats *out, bool traced)
+{
+    rbx_status st = enqueue_update(j, f, df, data, traced, 0);
+    if (st) return st;
+    return read_stats(j, 0, out, traced, true);
 }
 
 rbx_status rbx_update_from_tables(rbx_job *j, double f, double df, const void *data_dev, rbx_stats *out)
@@ -554,6 +569,153 @@ rbx_status rbx_update_frequency_host(rbx_job *j, double f, double df, const void
         CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     }
     return RBX_OK;
+}
+
+rbx_status rbx_update_frequency_async(rbx_job *j, double f, double df, const void *data_dev, int slot)
+{
+    if (!j || !data_dev) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_update_frequency_async before rbx_set_geometry");
+    NEED(j, !bad_freq(f) && std::isfinite(df) && df > 0, RBX_EINVAL, "frequency and spacing must be finite and > 0");
+    NEED(j, slot >= 0 && slot < kHistSlots, RBX_EINVAL, "stats slot must be in [0, 64)");
+    rbx_status st = rbx_trace_rays(j, f);
+    if (st) return st;
+    return enqueue_update(j, f, df, static_cast<const float2 *>(data_dev), true, slot);
+}
+
+rbx_status rbx_get_stats(rbx_job *j, int slot, rbx_stats *out)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_get_stats before rbx_set_geometry");
+    NEED(j, slot >= 0 && slot < kHistSlots, RBX_EINVAL, "stats slot must be in [0, 64)");
+    return read_stats(j, slot, out, true, false);
+}
+
+static double sweep_df(const double *freqs, int nf, int n)
+{
+    if (nf == 1) return 1e5;
+    if (n == 0) return freqs[1] - freqs[0];
+    if (n == nf - 1) return freqs[nf - 1] - freqs[nf - 2];
+    return 0.5 * (freqs[n + 1] - freqs[n - 1]);
+}
+
+// The whole sweep of one job on its stream, update n writing stats slot n.
+static rbx_status enqueue_sweep(rbx_job *j, const double *freqs, int nf, const void *data_dev)
+{
+    size_t nn = (size_t)j->w.N * j->w.N;
+    for (int n = 0; n < nf; n++) {
+        double df = sweep_df(freqs, nf, n);
+        NEED(j, std::isfinite(df) && df > 0, RBX_EINVAL, "frequencies must increase");
+        const float2 *d = static_cast<const float2 *>(data_dev) + (size_t)n * nn;
+        rbx_status st = rbx_update_frequency_async(j, freqs[n], df, d, n);
+        if (st) return st;
+    }
+    return RBX_OK;
+}
+
+rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs, const int *nf,
+                         const void *const *data_dev, int use_graph, rbx_stats *last, float *ms_total)
+{
+    if (!jobs || n < 1 || !freqs || !nf || !data_dev) return RBX_EINVAL;
+    for (int i = 0; i < n; i++) {
+        if (!jobs[i] || !freqs[i] || !data_dev[i] || nf[i] < 1) return RBX_EINVAL;
+        NEED(jobs[i], jobs[i]->has_geom, RBX_ESTATE, "rbx_batch_run on a job without geometry");
+        NEED(jobs[i], nf[i] <= kHistSlots, RBX_EINVAL, "at most 64 frequencies per job in a batch");
+        for (int k = 0; k < i; k++)
+            NEED(jobs[i], jobs[k] != jobs[i], RBX_EINVAL, "a job appears twice in the batch");
+    }
+    rbx_job *j0 = jobs[0];
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t *streams = new (std::nothrow) cudaStream_t[n]();
+    cudaEvent_t *joins = new (std::nothrow) cudaEvent_t[n]();
+    cudaStream_t *saved = new (std::nothrow) cudaStream_t[n]();
+    rbx_status st = RBX_OK;
+    bool capturing = false;
+    if (!streams || !joins || !saved) st = RBX_ENOMEM;
+#define BTRY(call)                                                                                       \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess && st == RBX_OK) st = fail(j0, RBX_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+    if (st == RBX_OK) {
+        BTRY(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+        BTRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        BTRY(cudaEventCreate(&t0));
+        BTRY(cudaEventCreate(&t1));
+        for (int i = 0; i < n && st == RBX_OK; i++) {
+            BTRY(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
+            BTRY(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming));
+            // wait for work already queued on the job's own stream, then run on the batch stream
+            BTRY(cudaStreamSynchronize(jobs[i]->stream));
+            saved[i] = jobs[i]->stream;
+            jobs[i]->stream = streams[i];
+        }
+    }
+    if (st == RBX_OK) {
+        if (use_graph) {
+            BTRY(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+            capturing = st == RBX_OK;
+        } else {
+            BTRY(cudaEventRecord(t0, origin));
+        }
+        BTRY(cudaEventRecord(fork, origin));
+        for (int i = 0; i < n && st == RBX_OK; i++) {
+            BTRY(cudaStreamWaitEvent(streams[i], fork, 0));
+            if (st == RBX_OK) {
+                rbx_status s2 = enqueue_sweep(jobs[i], freqs[i], nf[i], data_dev[i]);
+                if (s2 != RBX_OK) {
+                    st = s2;
+                    if (jobs[i] != j0) j0->err = jobs[i]->err;
+                }
+            }
+            BTRY(cudaEventRecord(joins[i], streams[i]));
+            BTRY(cudaStreamWaitEvent(origin, joins[i], 0));
+        }
+        if (capturing) {
+            cudaError_t e = cudaStreamEndCapture(origin, &graph);
+            if (e != cudaSuccess && st == RBX_OK) st = fail(j0, RBX_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            if (st == RBX_OK) BTRY(cudaGraphInstantiate(&exec, graph, 0));
+            if (st == RBX_OK) {
+                BTRY(cudaEventRecord(t0, origin));
+                BTRY(cudaGraphLaunch(exec, origin));
+            }
+        }
+        BTRY(cudaEventRecord(t1, origin));
+        BTRY(cudaStreamSynchronize(origin));
+    }
+    if (st == RBX_OK && ms_total) BTRY(cudaEventElapsedTime(ms_total, t0, t1));
+    for (int i = 0; i < n; i++) {
+        if (streams && saved && streams[i] && jobs[i]->stream == streams[i]) jobs[i]->stream = saved[i];
+        jobs[i]->ns_valid = false;
+    }
+    if (st == RBX_OK) {
+        for (int i = 0; i < n && st == RBX_OK; i++) {
+            rbx_job *j = jobs[i];
+            rbx_stats tmp;
+            rbx_status s2 = read_stats(j, nf[i] - 1, last ? &last[i] : &tmp, true, false);
+            if (s2 != RBX_OK) {
+                st = s2;
+                if (j != j0) j0->err = j->err;
+            }
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int i = 0; i < n; i++) {
+        if (streams && streams[i]) cudaStreamDestroy(streams[i]);
+        if (joins && joins[i]) cudaEventDestroy(joins[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (origin) cudaStreamDestroy(origin);
+    delete[] streams;
+    delete[] joins;
+    delete[] saved;
+#undef BTRY
+    return st;
 }
 
 rbx_status rbx_reconstruct(rbx_job *j, const double *freqs, int nf, const void *data_dev, rbx_stats *per_freq)

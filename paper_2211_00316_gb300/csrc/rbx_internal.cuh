@@ -12,6 +12,8 @@ constexpr int kFieldStride = 8;          // floats per node: n, n_x, n_y, n_xx, 
 constexpr uint32_t kUncovered = 0xFFFFFFFFu;
 constexpr int kMaxSteps = 2047;          // ray samples index i < 2048 (11 bits of the key)
 constexpr int kMaxXducers = 4095;        // ray index j < 4096 (12 bits of the key)
+constexpr int kHistSlots = 64;           // device history of per-update scalars (one slot per update)
+constexpr int kHistStride = 12;          // doubles per slot: |R|^2, sum dc^2, max|dc|, sum dm^2, counters[0..5], tc err
 
 // One (transducer, mask node) table entry, 16 bytes. The first 8 bytes, read as a
 // little-endian u64, are the ordering key (T bits, triangle id, K): the rasteriser keeps
@@ -60,6 +62,7 @@ struct Workspace {
     float2 *gdir = nullptr, *D = nullptr, *R = nullptr, *Rs = nullptr, *part = nullptr, *gpart = nullptr;
     float2 *data = nullptr;
     double *red = nullptr;           // reduction scratch
+    double *hist = nullptr;          // [kHistSlots][kHistStride] per-update scalars
     unsigned long long *counters = nullptr;   // [0] uncovered [1] clamped [2] bad rays [3] CAS bound [4] m <= 0 [5] bad model [6] mask count
     int fwd_splits = 1;
     TcPlanes tc;
@@ -116,6 +119,8 @@ void launch_combine_adjoint(const float2 *gpart, int X, int mode, int weight_mod
 void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X, int weight_mode, double f,
                    double df, double tau, double c0, float *c, double *red, unsigned long long *counters,
                    cudaStream_t s);
+void launch_snapshot(const double *r2, const double *upd3, const unsigned long long *counters, const unsigned *tc_err,
+                     double *slot, cudaStream_t s);
 int residual_blocks(int N);
 int update_blocks(int nx, int ny);
 

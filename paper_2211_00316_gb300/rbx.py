@@ -71,6 +71,10 @@ _SIGS = {
     "rbx_reconstruct": [_J, C.POINTER(C.c_double), C.c_int, _P, C.POINTER(Stats)],
     "rbx_synchronize": [_J],
     "rbx_destroy": [_J],
+    "rbx_update_frequency_async": [_J, C.c_double, C.c_double, _P, C.c_int],
+    "rbx_get_stats": [_J, C.c_int, C.POINTER(Stats)],
+    "rbx_batch_run": [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int),
+                      C.POINTER(C.c_void_p), C.c_int, C.POINTER(Stats), C.POINTER(C.c_float)],
     "rbx_forward_noalloc": [_P, _P, _P, _P, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, C.c_char_p,
                             C.c_size_t],
 }
@@ -227,5 +231,31 @@ class Job:
                                            sts))
         return [s.as_dict() for s in sts]
 
+    def update_frequency_async(self, f: float, df: float, data: torch.Tensor, slot: int = 0):
+        self._check(self.L.rbx_update_frequency_async(self.h, f, df, _ptr(data), slot))
+
+    def get_stats(self, slot: int = 0) -> dict:
+        st = Stats()
+        self._check(self.L.rbx_get_stats(self.h, slot, C.byref(st)))
+        return st.as_dict()
+
     def sync(self):
         self._check(self.L.rbx_synchronize(self.h))
+
+
+def batch_run(jobs: list, freqs: list, data: list, use_graph: bool = True):
+    """Batched form (rbx_batch_run): every job's sweep on its own stream, one CUDA graph.
+    Returns (per-job last-update stats, device milliseconds of the whole batch)."""
+    n = len(jobs)
+    L = load()
+    handles = (C.c_void_p * n)(*[j.h.value for j in jobs])
+    fr = [np.ascontiguousarray(f, dtype=np.float64) for f in freqs]
+    fptrs = (C.POINTER(C.c_double) * n)(*[f.ctypes.data_as(C.POINTER(C.c_double)) for f in fr])
+    nf = (C.c_int * n)(*[len(f) for f in fr])
+    dptrs = (C.c_void_p * n)(*[_ptr(d) for d in data])
+    last = (Stats * n)()
+    ms = C.c_float(0.0)
+    st = L.rbx_batch_run(handles, n, fptrs, nf, dptrs, int(use_graph), last, C.byref(ms))
+    if st != 0:
+        raise RbxError(st, L.rbx_last_error(jobs[0].h).decode())
+    return [s.as_dict() for s in last], ms.value
