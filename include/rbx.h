@@ -210,6 +210,64 @@ rbx_status rbx_forward_noalloc(const float *T_dev, const float *a_dev, const uin
                                int n_xducers, int n_nodes, double freq_hz, double c0, void *D_dev, void *cuda_stream,
                                char *err, size_t errlen);
 
+/* ---------------------------------------------------------------- served form
+ * A server takes reconstruction requests (host buffers) at any time and runs them with
+ * continuous batching: a worker thread admits queued requests in arrival order while their
+ * estimated device memory fits hbm_budget_bytes and fewer than max_inflight run; each runs its
+ * whole low-to-high sweep (Sec. 3.4) on a stream of its own with data and model resident on
+ * the device, overlapping the others; finished requests release their memory, which admits
+ * the next. Results are the same as running each request alone. The server uses the CUDA
+ * device current when it is created. */
+typedef struct rbx_server rbx_server;
+
+typedef enum {
+    RBX_REQ_QUEUED = 0,
+    RBX_REQ_RUNNING = 1,
+    RBX_REQ_DONE = 2,
+    RBX_REQ_FAILED = 3,
+    RBX_REQ_CANCELLED = 4
+} rbx_request_state;
+
+rbx_status rbx_server_create(rbx_server **out, size_t hbm_budget_bytes, int max_inflight);
+
+/* The server's admission estimate of the device bytes one request of this geometry and
+ * nf frequencies reserves (an upper estimate of a job's workspaces plus its data). */
+size_t rbx_estimate_bytes(const rbx_geometry *geom, int nf);
+
+/* Queue a request: geometry, initial model c_init_host (ny*nx float32), frequencies
+ * freqs_host[0..nf-1] (increasing, nf <= 64) and data_host (nf blocks of N x N complex64).
+ * The inputs are copied; *ticket identifies the request. A request whose estimated memory
+ * exceeds the budget fails with RBX_ENOMEM when it reaches the head of the queue. */
+rbx_status rbx_server_submit(rbx_server *srv, const rbx_geometry *geom, const float *c_init_host,
+                             const double *freqs_host, int nf, const void *data_host, long long *ticket);
+
+/* State of a request (rbx_request_state). Once it has ended: latency_s = seconds from
+ * submission to completion, and for a finished request c_out_host (ny*nx float32, nullable)
+ * and last (nullable, scalars of its last update). Returns the request's final status once it
+ * has ended (RBX_OK while it is queued or running). */
+rbx_status rbx_server_poll(rbx_server *srv, long long ticket, int *state, double *latency_s, float *c_out_host,
+                           rbx_stats *last);
+
+/* Block until the request has ended or timeout_s passes (RBX_ETIMEOUT). */
+rbx_status rbx_server_wait(rbx_server *srv, long long ticket, double timeout_s);
+
+/* Cancel a request that is still queued (RBX_ESTATE once it runs). */
+rbx_status rbx_server_cancel(rbx_server *srv, long long ticket);
+
+/* Host-clock times of a request, in seconds since the server was created: submission,
+ * admission (start of its device work; -1 while queued or if it never started) and end
+ * (-1 while it has not ended). */
+rbx_status rbx_server_times(rbx_server *srv, long long ticket, double *t_submit, double *t_start, double *t_end);
+
+/* Requests queued and running, and the device bytes reserved by running ones. */
+rbx_status rbx_server_info(rbx_server *srv, int *queued, int *running, size_t *bytes_in_use);
+
+/* Error message of an ended request ("" if none); valid while the server exists. */
+const char *rbx_server_error(rbx_server *srv, long long ticket);
+
+/* Finish running requests, cancel queued ones, stop the worker and free the server. */
+rbx_status rbx_server_destroy(rbx_server *srv);
+
 /* Last error message of the job ("" if none). The string lives as long as the job. */
 const char *rbx_last_error(const rbx_job *job);
 

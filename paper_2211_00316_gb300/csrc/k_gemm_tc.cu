@@ -501,7 +501,7 @@ bool make_map(CUtensorMap *m, const void *base, size_t rows, size_t cols)
 
 // ---------------------------------------------------------------- API used by rbx_api.cu
 
-bool tc_setup(TcPlanes &p, int N, int X, bool split)
+bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t st)
 {
     p.split = split;
     const int mult = split ? 2 : 1;
@@ -526,15 +526,17 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split)
     const size_t fbytes = mult * 4 * p.fwd_pstride * sizeof(__nv_bfloat16);
     const size_t bbytes = mult * 6 * p.bp_pstride * sizeof(__nv_bfloat16);
     const size_t rbytes = mult * 2 * (size_t)p.Npad * p.Npad * sizeof(__nv_bfloat16);
-    if (cudaMalloc(&p.fplanes, fbytes) != cudaSuccess) return false;
-    if (cudaMalloc(&p.bplanes, bbytes) != cudaSuccess) return false;
-    if (cudaMalloc(&p.rsplanes, rbytes) != cudaSuccess) return false;
-    if (cudaMalloc(&p.bpart, (size_t)(p.Npad / BN) * p.Xp * sizeof(float2)) != cudaSuccess) return false;
-    if (cudaMalloc(&p.err, sizeof(unsigned)) != cudaSuccess) return false;
-    cudaMemset(p.fplanes, 0, fbytes);
-    cudaMemset(p.bplanes, 0, bbytes);
-    cudaMemset(p.rsplanes, 0, rbytes);
-    cudaMemset(p.err, 0, sizeof(unsigned));
+    if (cudaMallocAsync(&p.fplanes, fbytes, st) != cudaSuccess) return false;
+    if (cudaMallocAsync(&p.bplanes, bbytes, st) != cudaSuccess) return false;
+    if (cudaMallocAsync(&p.rsplanes, rbytes, st) != cudaSuccess) return false;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&p.bpart), (size_t)(p.Npad / BN) * p.Xp * sizeof(float2), st) !=
+        cudaSuccess)
+        return false;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&p.err), sizeof(unsigned), st) != cudaSuccess) return false;
+    cudaMemsetAsync(p.fplanes, 0, fbytes, st);
+    cudaMemsetAsync(p.bplanes, 0, bbytes, st);
+    cudaMemsetAsync(p.rsplanes, 0, rbytes, st);
+    cudaMemsetAsync(p.err, 0, sizeof(unsigned), st);
     const __nv_bfloat16 *f = static_cast<const __nv_bfloat16 *>(p.fplanes);
     const __nv_bfloat16 *b = static_cast<const __nv_bfloat16 *>(p.bplanes);
     const __nv_bfloat16 *r = static_cast<const __nv_bfloat16 *>(p.rsplanes);
@@ -559,11 +561,11 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split)
     return ok;
 }
 
-void tc_free(TcPlanes &p)
+void tc_free(TcPlanes &p, cudaStream_t st)
 {
     void *ps[] = {p.fplanes, p.bplanes, p.rsplanes, p.bpart, p.err};
     for (void *q : ps)
-        if (q) cudaFree(q);
+        if (q) cudaFreeAsync(q, st);
     p = TcPlanes{};
 }
 

@@ -4,9 +4,11 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 using namespace rbx;
 
@@ -57,19 +59,35 @@ static rbx_status fail(rbx_job *j, rbx_status st, const char *fmt, ...)
         if (!(cond)) return fail(job, st, "%s", msg);                                        \
     } while (0)
 
-template <class T>
-static cudaError_t dalloc(T *&p, size_t n)
+// Job workspaces come from the device's stream-ordered pool: allocating and releasing them
+// never waits for other jobs' work (a plain cudaFree would synchronise the whole device).
+// The pool keeps released memory for reuse (release threshold raised once per device).
+static void keep_pool_memory()
 {
-    return cudaMalloc(reinterpret_cast<void **>(&p), (n ? n : 1) * sizeof(T));
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[dev] = true;
 }
 
-static void free_ws(Workspace &w)
+template <class T>
+static cudaError_t dalloc(T *&p, size_t n, cudaStream_t s)
+{
+    return cudaMallocAsync(reinterpret_cast<void **>(&p), (n ? n : 1) * sizeof(T), s);
+}
+
+static void free_ws(Workspace &w, cudaStream_t s)
 {
     void *ps[] = {w.hist, w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
                   w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters};
     for (void *p : ps)
-        if (p) cudaFree(p);
-    tc_free(w.tc);
+        if (p) cudaFreeAsync(p, s);
+    tc_free(w.tc, s);
     w = Workspace{};
 }
 
@@ -122,8 +140,9 @@ rbx_status rbx_destroy(rbx_job *j)
 {
     if (!j) return RBX_EINVAL;
     cudaStreamSynchronize(j->stream);
-    free_ws(j->w);
-    if (j->d_count) cudaFree(j->d_count);
+    free_ws(j->w, j->stream);
+    if (j->d_count) cudaFreeAsync(j->d_count, j->stream);
+    cudaStreamSynchronize(j->stream);
     for (int k = 0; k < EV_COUNT; k++)
         if (j->ev[k]) cudaEventDestroy(j->ev[k]);
     if (j->own_stream) cudaStreamDestroy(j->stream);
@@ -162,19 +181,20 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     NEED(j, (double)g.nx * g.ny < 2e9, RBX_EINVAL, "grid too large");
 
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
-    free_ws(j->w);
+    free_ws(j->w, j->stream);
+    keep_pool_memory();
     j->has_geom = j->has_tables = j->ns_valid = false;
     Workspace &w = j->w;
     w.N = g.n_xducers;
     w.nx = g.nx;
     w.ny = g.ny;
     const size_t nxy = (size_t)g.nx * g.ny, N = w.N;
-    if (!j->d_count) CUDA_TRY(j, dalloc(j->d_count, 1));
+    if (!j->d_count) CUDA_TRY(j, dalloc(j->d_count, 1, j->stream));
 #define ALLOC(p, n)                                                                                   \
     do {                                                                                              \
-        if (dalloc(p, n) != cudaSuccess) {                                                            \
+        if (dalloc(p, n, j->stream) != cudaSuccess) {                                                 \
             cudaGetLastError();                                                                       \
-            free_ws(w);                                                                               \
+            free_ws(w, j->stream);                                                                    \
             return fail(j, RBX_ENOMEM, "device allocation of %s (%zu elements) failed", #p, (size_t)(n)); \
         }                                                                                             \
     } while (0)
@@ -210,9 +230,9 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     ALLOC(w.Rs, N * N);
     ALLOC(w.data, N * N);
     if (g.precision != RBX_FP32) {
-        if (!tc_setup(w.tc, w.N, X, g.precision == RBX_BF16X3)) {
+        if (!tc_setup(w.tc, w.N, X, g.precision == RBX_BF16X3, j->stream)) {
             cudaGetLastError();
-            free_ws(w);
+            free_ws(w, j->stream);
             return fail(j, RBX_ENOMEM, "tensor-core operand set-up failed (allocation or TMA descriptor)");
         }
         if (w.tc.fwd_splits > w.fwd_splits) w.fwd_splits = w.tc.fwd_splits;
@@ -523,6 +543,31 @@ static rbx_status read_stats(rbx_job *j, int slot, rbx_stats *out, bool traced, 
     return RBX_OK;
 }
 
+// Status of a whole sweep: the first failing update among slots 0..nf-1 decides it (a later
+// update starts from the kept model and may itself succeed); `out` gets the last slot.
+static rbx_status read_sweep(rbx_job *j, int nf, rbx_stats *out)
+{
+    Workspace &w = j->w;
+    std::vector<double> h((size_t)nf * kHistStride);
+    CUDA_TRY(j, cudaMemcpyAsync(h.data(), w.hist, h.size() * sizeof(double), cudaMemcpyDeviceToHost, j->stream));
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    for (int s = 0; s < nf - 1; s++) {
+        const double *hs = h.data() + (size_t)s * kHistStride;
+        if (hs[10] != 0 || hs[8] != 0 || hs[6] != 0 || hs[7] != 0) {
+            rbx_status st = read_stats(j, s, nullptr, true, false);
+            if (st != RBX_OK) {
+                char msg[64];
+                std::snprintf(msg, sizeof msg, " (update %d of %d)", s + 1, nf);
+                std::string keep = j->err + msg;
+                if (out) read_stats(j, nf - 1, out, true, false);
+                j->err = keep;
+                return st;
+            }
+        }
+    }
+    return read_stats(j, nf - 1, out, true, false);
+}
+
 static rbx_status update_core(rbx_job *j, double f, double df, const float2 *data, rbx_stats *out, bool traced)
 {
     rbx_status st = enqueue_update(j, f, df, data, traced, 0);
@@ -694,7 +739,7 @@ rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs
         for (int i = 0; i < n && st == RBX_OK; i++) {
             rbx_job *j = jobs[i];
             rbx_stats tmp;
-            rbx_status s2 = read_stats(j, nf[i] - 1, last ? &last[i] : &tmp, true, false);
+            rbx_status s2 = read_sweep(j, nf[i], last ? &last[i] : &tmp);
             if (s2 != RBX_OK) {
                 st = s2;
                 if (j != j0) j0->err = j->err;
@@ -717,6 +762,42 @@ rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs
 #undef BTRY
     return st;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- hooks for the server (C++)
+namespace rbx {
+rbx_status job_enqueue_sweep(rbx_job *j, const double *freqs, int nf, const void *data_dev)
+{
+    for (int n = 0; n < nf; n++)
+        if (!(std::isfinite(freqs[n]) && freqs[n] > 0)) return fail(j, RBX_EINVAL, "frequencies must be finite and > 0");
+    NEED(j, nf <= kHistSlots, RBX_EINVAL, "at most 64 frequencies per request");
+    return enqueue_sweep(j, freqs, nf, data_dev);
+}
+rbx_status job_read_sweep(rbx_job *j, int nf, rbx_stats *last) { return read_sweep(j, nf, last); }
+cudaStream_t job_stream(const rbx_job *j) { return j->stream; }
+float *job_model(rbx_job *j) { return j->w.c; }
+
+// Upper estimate of the device bytes one job needs (admission control).
+size_t job_bytes_estimate(const rbx_geometry &g, int nf)
+{
+    const double r = g.mask_radius / g.dx;
+    const size_t X = (size_t)(3.14159265358979 * r * r + 6.3 * r + 16);
+    const size_t N = (size_t)g.n_xducers, NX = N * X, nxy = (size_t)g.nx * g.ny, NN = N * N;
+    size_t b = NX * (16 + 4 + 8);                                 // tables, angular density, G
+    if (g.precision == RBX_FP32) b += NX * 16;                    // U, kappa
+    else {
+        const size_t Np = (N + 127) / 128 * 128, Xk = (X + 63) / 64 * 64, Xm = (X + 127) / 128 * 128;
+        const size_t m = g.precision == RBX_BF16X3 ? 2 : 1;
+        b += m * (4 * Np * Xk + 6 * Xm * Np + 2 * Np * Np) * 2 + (Np / 128) * Xm * 8;
+    }
+    b += nxy * (4 + 4 + 8 + 8 + 32 + 4 + 4) + N * (N - 1) * 16 + NN * 8 * 5 + 64 * NN * 8 + X * 24;
+    b += (size_t)nf * NN * 8 + nxy * 4 + (1u << 20);              // data, initial model, slack
+    return b;
+}
+}  // namespace rbx
+
+extern "C" {
 
 rbx_status rbx_reconstruct(rbx_job *j, const double *freqs, int nf, const void *data_dev, rbx_stats *per_freq)
 {

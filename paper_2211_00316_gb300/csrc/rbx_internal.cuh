@@ -103,8 +103,8 @@ void launch_backproject_simt(const float2 *A, const float2 *kap, const float2 *R
                              float2 *gpart, cudaStream_t s);
 
 // k_gemm_tc.cu (BF16 tensor cores)
-bool tc_setup(TcPlanes &p, int N, int X, bool split);
-void tc_free(TcPlanes &p);
+bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t s);
+void tc_free(TcPlanes &p, cudaStream_t s);
 int launch_forward_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, float2 *part,
                       cudaStream_t s);
 void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, double f, double c0, cudaStream_t s);
@@ -123,5 +123,12 @@ void launch_snapshot(const double *r2, const double *upd3, const unsigned long l
                      double *slot, cudaStream_t s);
 int residual_blocks(int N);
 int update_blocks(int nx, int ny);
+
+// rbx_api.cu: hooks for the server (C++ linkage, not part of the C ABI)
+rbx_status job_enqueue_sweep(rbx_job *j, const double *freqs, int nf, const void *data_dev);
+rbx_status job_read_sweep(rbx_job *j, int nf, rbx_stats *last);
+cudaStream_t job_stream(const rbx_job *j);
+float *job_model(rbx_job *j);
+size_t job_bytes_estimate(const rbx_geometry &g, int nf);
 
 }  // namespace rbx

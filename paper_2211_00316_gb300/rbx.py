@@ -75,13 +75,28 @@ _SIGS = {
     "rbx_get_stats": [_J, C.c_int, C.POINTER(Stats)],
     "rbx_batch_run": [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int),
                       C.POINTER(C.c_void_p), C.c_int, C.POINTER(Stats), C.POINTER(C.c_float)],
+    "rbx_server_create": [C.POINTER(C.c_void_p), C.c_size_t, C.c_int],
+    "rbx_server_submit": [_P, C.POINTER(Geometry), _P, C.POINTER(C.c_double), C.c_int, _P,
+                          C.POINTER(C.c_longlong)],
+    "rbx_server_poll": [_P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double), _P, C.POINTER(Stats)],
+    "rbx_server_wait": [_P, C.c_longlong, C.c_double],
+    "rbx_server_cancel": [_P, C.c_longlong],
+    "rbx_server_times": [_P, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "rbx_server_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
+    "rbx_server_destroy": [_P],
     "rbx_forward_noalloc": [_P, _P, _P, _P, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, C.c_char_p,
                             C.c_size_t],
 }
 
 
 def exported_symbols() -> list[str]:
-    return list(_SIGS) + ["rbx_last_error"]
+    return list(_SIGS) + ["rbx_last_error", "rbx_server_error", "rbx_estimate_bytes"]
+
+
+def estimate_bytes(g, nf: int, precision: int = RBX_BF16) -> int:
+    """Device bytes the server reserves for one request of this geometry (rbx_estimate_bytes)."""
+    G = geometry_struct(g, precision)
+    return int(load().rbx_estimate_bytes(C.byref(G), int(nf)))
 
 
 def load(path: str | None = None):
@@ -99,6 +114,10 @@ def load(path: str | None = None):
                 f.restype = C.c_int
             L.rbx_last_error.argtypes = [_J]
             L.rbx_last_error.restype = C.c_char_p
+            L.rbx_server_error.argtypes = [_P, C.c_longlong]
+            L.rbx_server_error.restype = C.c_char_p
+            L.rbx_estimate_bytes.argtypes = [C.POINTER(Geometry), C.c_int]
+            L.rbx_estimate_bytes.restype = C.c_size_t
             _lib = L
     return _lib
 
@@ -259,3 +278,73 @@ def batch_run(jobs: list, freqs: list, data: list, use_graph: bool = True):
     if st != 0:
         raise RbxError(st, L.rbx_last_error(jobs[0].h).decode())
     return [s.as_dict() for s in last], ms.value
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+
+
+def geometry_struct(g, precision: int = RBX_FP32, weight_mode: int | None = None, tau: float | None = None):
+    return Geometry(g.nx, g.ny, g.dx, g.x0, g.y0, g.n_xducers, g.ring_radius, g.mask_radius, g.c0, g.ds,
+                    g.weight_mode if weight_mode is None else weight_mode, g.tau if tau is None else tau, precision)
+
+
+class Server:
+    """Served form (rbx_server_*): continuous batching of reconstruction requests."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 8):
+        self.L = load()
+        self.h = C.c_void_p()
+        st = self.L.rbx_server_create(C.byref(self.h), int(hbm_budget_bytes), int(max_inflight))
+        if st != 0:
+            raise RbxError(st, "server creation failed")
+
+    def submit(self, g, c_init, freqs, data, precision: int = RBX_BF16) -> int:
+        """g: phantoms.Geometry; c_init (ny, nx) array; freqs (nf,); data (nf, N, N) complex."""
+        G = geometry_struct(g, precision)
+        c = np.ascontiguousarray(c_init, dtype=np.float32)
+        fr = np.ascontiguousarray(freqs, dtype=np.float64)
+        d = np.ascontiguousarray(data, dtype=np.complex64)
+        t = C.c_longlong()
+        st = self.L.rbx_server_submit(self.h, C.byref(G), c.ctypes.data, fr.ctypes.data_as(C.POINTER(C.c_double)),
+                                      len(fr), d.ctypes.data, C.byref(t))
+        if st != 0:
+            raise RbxError(st, "submit failed")
+        return t.value
+
+    def poll(self, ticket: int, want_model: bool = False, shape=None):
+        state, lat, last = C.c_int(), C.c_double(-1.0), Stats()
+        out = np.empty(shape, np.float32) if want_model else None
+        st = self.L.rbx_server_poll(self.h, ticket, C.byref(state), C.byref(lat),
+                                    out.ctypes.data if out is not None else None, C.byref(last))
+        return dict(state=state.value, status=st, latency_s=lat.value, model=out, last=last.as_dict(),
+                    error=self.L.rbx_server_error(self.h, ticket).decode())
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> int:
+        return self.L.rbx_server_wait(self.h, ticket, timeout_s)
+
+    def cancel(self, ticket: int) -> int:
+        return self.L.rbx_server_cancel(self.h, ticket)
+
+    def times(self, ticket: int):
+        """Seconds since server creation: submitted, started (-1 if not), ended (-1 if not)."""
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        st = self.L.rbx_server_times(self.h, ticket, C.byref(a), C.byref(b), C.byref(c))
+        if st != 0:
+            raise RbxError(st, "unknown ticket")
+        return dict(submit=a.value, start=b.value, end=c.value)
+
+    def info(self):
+        q, r, b = C.c_int(), C.c_int(), C.c_size_t()
+        self.L.rbx_server_info(self.h, C.byref(q), C.byref(r), C.byref(b))
+        return dict(queued=q.value, running=r.value, bytes_in_use=b.value)
+
+    def close(self):
+        if self.h:
+            self.L.rbx_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -68,3 +68,16 @@ def test_async_stats_match_sync():
     with pytest.raises(rbx.RbxError):
         j.get_stats(64)
     j.close()
+
+
+def test_batch_reports_a_failure_inside_the_sweep():
+    """A non-finite datum at the second frequency fails that update (the model is kept) and the
+    later updates succeed; the batch must still report the failure."""
+    ws = slices()[:2]
+    jobs, data = prepare(ws, rbx.RBX_BF16)
+    data[1][1, 3, 7] = complex(float("nan"), 0.0)
+    with pytest.raises(rbx.RbxError) as e:
+        rbx.batch_run(jobs, [w.freqs for w in ws], data, use_graph=True)
+    assert e.value.status == 5 and "update 2 of 3" in str(e.value)
+    for j in jobs:
+        j.close()
