@@ -212,19 +212,232 @@ def run_reference(args):
     return 0
 
 
+def slice_pool(n_slices: int, rbx, P, torch) -> list:
+    """The uneven slices of the batched workload (seeds 0..n-1) with their data: the library's
+    FP32 ray-Born prediction on each true model plus 40 dB noise, as host arrays."""
+    pool = []
+    for s in range(n_slices):
+        w = P.batched_slice(s)
+        j = rbx.Job()
+        j.set_geometry(w.geom, precision=rbx.RBX_FP32)
+        j.set_model(torch.tensor(w.c_true, dtype=torch.float32, device="cuda"))
+        d = []
+        for f in w.freqs:
+            j.trace_rays(float(f))
+            d.append(j.predict(float(f)).cpu().numpy())
+        j.close()
+        pool.append((w, P.add_noise(np.stack(d), w.snr_db, seed=200 + s).astype(np.complex64)))
+    return pool
+
+
+def batched_form(args, rbx, P, torch) -> dict:
+    """32 independent slices of uneven size, each a full 10-frequency sweep (320 updates per
+    step): one CUDA graph of all sweeps (BF16), the same work as plain multi-stream launches,
+    and the plain per-job forms (each job's sweep after the other's, synchronising per update)
+    in BF16 and FP32."""
+    pool = slice_pool(args.slices, rbx, P, torch)
+    freqs = [w.freqs for w, _ in pool]
+    updates = sum(len(f) for f in freqs)
+    out = {"updates_per_step": updates}
+    models = {}
+
+    def make(prec):
+        jobs, data = [], []
+        for w, d in pool:
+            j = rbx.Job()
+            j.set_geometry(w.geom, precision=prec)
+            jobs.append(j)
+            data.append(torch.tensor(d, device="cuda"))
+        est = sum(rbx.estimate_bytes(w.geom, len(w.freqs), prec) for w, _ in pool)
+        return jobs, data, est
+
+    def reset(jobs):
+        for (w, _), j in zip(pool, jobs):
+            j.set_model(torch.tensor(w.c_init, dtype=torch.float32, device="cuda"))
+
+    def timed(name, jobs, run):
+        for _ in range(args.warmup):
+            reset(jobs)
+            run()
+        dev, wall = [], []
+        for _ in range(args.steps):
+            reset(jobs)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ms = run()
+            torch.cuda.synchronize()
+            wall.append(time.perf_counter() - t0)
+            dev.append(ms / 1e3 if ms is not None else wall[-1])
+        models[name] = [j.get_model().cpu().numpy() for j in jobs]
+        out[name] = {"value": updates / float(np.mean(dev)), "unit": UNIT, "s_per_step_device": float(np.mean(dev)),
+                     "s_per_step_wall": float(np.mean(wall))}
+
+    def sequential(jobs, data):
+        def run():
+            for w, j, d in zip(pool, jobs, data):
+                j.reconstruct(w[0].freqs, d)
+        return run
+
+    for prec, tag in ((rbx.RBX_BF16, "bf16"), (rbx.RBX_FP32, "fp32")):
+        used0 = rbx.pool_usage(trim=True)["used"]
+        jobs, data, est = make(prec)
+        data_bytes = sum(d.numel() * d.element_size() for d in data)
+        used1 = rbx.pool_usage()["used"]
+        reset(jobs)
+        batch_run = lambda g: (lambda: rbx.batch_run(jobs, freqs, data, use_graph=g)[1])
+        timed(f"graph_{tag}", jobs, batch_run(True))
+        if tag == "bf16":
+            timed(f"streams_{tag}", jobs, batch_run(False))
+        timed(f"sequential_{tag}", jobs, sequential(jobs, data))
+        out[f"device_bytes_{tag}"] = {"jobs_measured": int(used1 - used0 + data_bytes), "estimate": int(est)}
+        for j in jobs:
+            j.close()
+        del data
+        torch.cuda.empty_cache()
+    # agreement of the BF16 graph form with the plain FP32 form after the whole sweep
+    diffs = [float(np.sqrt(np.mean((a - b) ** 2))) for a, b in zip(models["graph_bf16"], models["sequential_fp32"])]
+    same = all(np.array_equal(a, b) for a, b in zip(models["graph_bf16"], models["sequential_bf16"]))
+    out["rms_dc_bf16_vs_fp32_m_s"] = {"max": max(diffs), "median": float(np.median(diffs))}
+    # error against the true model on the mask after the sweep, per slice: initial, BF16, FP32
+    errs = []
+    for k, (w, _) in enumerate(pool):
+        mk = w.geom.mask()
+        e = [float(np.sqrt(np.mean((x[mk] - w.c_true[mk]) ** 2)))
+             for x in (w.c_init, models["graph_bf16"][k], models["sequential_fp32"][k])]
+        errs.append([w.name] + [round(v, 4) for v in e] + [round(diffs[k], 4)])
+    out["rms_vs_true_m_s"] = {"columns": ["slice", "initial", "bf16_graph", "fp32_plain", "bf16_vs_fp32"], "rows": errs}
+    out["graph_equals_sequential_bf16"] = bool(same)
+    out["slices"] = [f"{w.name} dx={w.geom.dx*1e3:.2f}mm" for w, _ in pool]
+    return out
+
+
+def served_form(rbx, P, torch, pool, n_req: int, rate: float, budget: float, max_inflight: int, closed: int,
+                serial_fp32: bool) -> dict:
+    """Poisson arrivals (seeded) of reconstruction requests drawn from the slice pool, each a full
+    sweep, submitted to the library's server; latency = submission to completion (server clock).
+    Also a closed-loop burst (all requests at once: maximum throughput) and, optionally, the same
+    arrival stream served by the plain per-job FP32 form one request after the other."""
+    rng = np.random.default_rng(5)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    res = {"requests": n_req, "rate_req_s": rate, "hbm_budget_gb": budget / 1e9, "max_inflight": max_inflight}
+
+    def pct(lat):
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(np.mean(lat)), "max_s": float(np.max(lat))}
+
+    srv = rbx.Server(int(budget), max_inflight)
+    warm = [srv.submit(w.geom, w.c_init, w.freqs, d) for w, d in pool[:4]]
+    for t in warm:
+        assert srv.wait(t, 600.0) == 0
+    t0 = time.perf_counter()
+    tickets = []
+    for k in range(n_req):
+        dt = t0 + arrivals[k] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        w, d = pool[k % len(pool)]
+        tickets.append(srv.submit(w.geom, w.c_init, w.freqs, d))
+    for t in tickets:
+        assert srv.wait(t, 600.0) == 0, srv.poll(t)["error"]
+    tm = [srv.times(t) for t in tickets]
+    ups = sum(len(pool[k % len(pool)][0].freqs) for k in range(n_req))
+    span = max(x["end"] for x in tm) - min(x["submit"] for x in tm)
+    res["open_loop"] = dict(pct([x["end"] - x["submit"] for x in tm]),
+                            queue_wait_p99_s=float(np.percentile([x["start"] - x["submit"] for x in tm], 99)),
+                            updates_per_s=ups / span)
+    if closed > 0:
+        tk = [srv.submit(*(lambda w, d: (w.geom, w.c_init, w.freqs, d))(*pool[k % len(pool)])) for k in range(closed)]
+        for t in tk:
+            assert srv.wait(t, 600.0) == 0
+        tm = [srv.times(t) for t in tk]
+        ups = sum(len(pool[k % len(pool)][0].freqs) for k in range(closed))
+        span = max(x["end"] for x in tm) - min(x["submit"] for x in tm)
+        res["closed_loop"] = dict(pct([x["end"] - x["submit"] for x in tm]), requests=closed, updates_per_s=ups / span)
+    srv.close()
+    if serial_fp32:
+        lat, busy = [], 0.0
+        t0 = time.perf_counter()
+        for k in range(n_req):
+            dt = t0 + arrivals[k] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            w, d = pool[k % len(pool)]
+            ts = time.perf_counter()
+            j = rbx.Job()
+            j.set_geometry(w.geom, precision=rbx.RBX_FP32)
+            j.set_model(torch.tensor(w.c_init, dtype=torch.float32).cuda())
+            j.reconstruct(w.freqs, torch.tensor(d).cuda())
+            j.get_model().cpu()
+            j.close()
+            te = time.perf_counter()
+            busy += te - ts
+            lat.append(te - (t0 + arrivals[k]))
+        ups = sum(len(pool[k % len(pool)][0].freqs) for k in range(n_req))
+        res["serial_plain_fp32"] = dict(pct(lat), updates_per_s_busy=ups / busy)
+    return res
+
+
+def run_forms(args) -> int:
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2211_00316_gb300 import build as B
+    B.build()
+    from paper_2211_00316_gb300 import phantoms as P
+    from paper_2211_00316_gb300 import rbx
+    clocks = Clocks(0)
+    if args.workload == "batched_slices32":
+        r = batched_form(args, rbx, P, torch)
+        clk = clocks.stop()
+        line = {"metric": "ray-Born freq-updates/s, 32 uneven slices, full 10-frequency sweeps",
+                "value": r["graph_bf16"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["graph_bf16"]["s_per_step_device"] * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "data": "synthetic (library FP32 ray-Born prediction on seeded breast-like slices + 40 dB noise)",
+                "config": {"workload": f"{args.slices} slices: N in {{256,512,768,1024}}, grids 192-512 at "
+                                       "0.45-1.0 mm, seeds 0-31, 100 kHz-1 MHz", "form": "one CUDA graph, BF16",
+                           "l2": "inputs larger than L2"},
+                "clocks": clk, "forms": r}
+    else:
+        pool = slice_pool(args.slices, rbx, P, torch)
+        r = served_form(rbx, P, torch, pool, args.requests, args.rate, args.budget_gb * 1e9, args.max_inflight,
+                        args.closed, not args.no_serial)
+        clk = clocks.stop()
+        line = {"metric": "p50/p99 request latency, Poisson arrivals", "value": r["open_loop"]["p50_s"], "unit": "s",
+                "n_gpus": 1, "higher_is_better": False, "dtype": "bf16",
+                "data": "synthetic (library FP32 ray-Born prediction on seeded breast-like slices + 40 dB noise)",
+                "config": {"workload": f"{args.requests} requests at {args.rate} req/s drawn from {args.slices} "
+                                       "uneven slices, 10-frequency sweeps", "hbm_budget_gb": args.budget_gb},
+                "clocks": clk, "serve": r}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rbx", choices=["rbx", "reference"])
-    ap.add_argument("--workload", default="precision_ring1024", choices=["precision_ring1024", "fp32_ring256", "ring1024_grid288", "small"])
+    ap.add_argument("--workload", default="precision_ring1024",
+                    choices=["precision_ring1024", "fp32_ring256", "ring1024_grid288", "small", "batched_slices32",
+                             "served_poisson"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--slices", type=int, default=32, help="batched/served forms: slices in the pool")
+    ap.add_argument("--requests", type=int, default=500, help="served form: Poisson requests")
+    ap.add_argument("--rate", type=float, default=4.0, help="served form: arrivals per second")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="served form: HBM admission budget")
+    ap.add_argument("--max-inflight", type=int, default=16)
+    ap.add_argument("--closed", type=int, default=64, help="served form: closed-loop burst size (0 = none)")
+    ap.add_argument("--no-serial", action="store_true", help="served form: skip the serial plain FP32 replay")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="default workload: requests of the short served run reported beside throughput (0 = none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("batched_slices32", "served_poisson"):
+        return run_forms(args)
 
     import torch
     import torch.distributed as dist
@@ -309,6 +522,15 @@ def main():
                    "d2h_bytes_per_step": g.nx * g.ny * 4}
         job.close()
 
+    # request latency of the served form: a short seeded Poisson stream of uneven requests
+    serve = None
+    if args.serve_requests > 0:
+        torch.cuda.empty_cache()
+        pool = slice_pool(args.slices, rbx, P, torch)
+        serve = served_form(rbx, P, torch, pool, args.serve_requests, args.rate, args.budget_gb * 1e9,
+                            args.max_inflight, args.serve_requests, False)
+        del pool
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -348,6 +570,12 @@ def main():
             "kernel_ms": kms, "stage_ms": {k: float(np.mean([s[k] for s in stats]))
                                            for k in ("ms_trace", "ms_forward", "ms_backproj", "ms_total")},
             "n_uncovered": int(stats[-1]["n_uncovered"]), "rms_dc_last": stats[-1]["rms_dc"]}
+    if serve is not None:
+        line["latency"] = {"p50_s": serve["open_loop"]["p50_s"], "p99_s": serve["open_loop"]["p99_s"],
+                           "requests": serve["requests"], "rate_req_s": serve["rate_req_s"],
+                           "workload": f"Poisson arrivals of 10-frequency sweeps drawn from {args.slices} uneven "
+                                       "slices (N 256-1024, grids 192-512), BF16, served form"}
+        line["serve"] = serve
     if not args.no_cpu_baseline and world == 1:
         cb = cpu_baseline(w, float(w.freqs[0]))
         cb.pop("seconds_per_update", None)

@@ -271,6 +271,12 @@ rbx_status rbx_server_destroy(rbx_server *srv);
 /* Last error message of the job ("" if none). The string lives as long as the job. */
 const char *rbx_last_error(const rbx_job *job);
 
+/* Device memory of the stream-ordered pool all jobs of the current device allocate from:
+ * bytes held by live allocations (used) and bytes the pool has taken from the device
+ * (reserved; freed workspaces stay reserved for reuse). trim != 0 first returns the unused
+ * reserve to the device (after synchronising the device). Either pointer may be NULL. */
+rbx_status rbx_pool_usage(size_t *used, size_t *reserved, int trim);
+
 /* Wait for all work queued on the job's stream. */
 rbx_status rbx_synchronize(rbx_job *job);
 

@@ -799,6 +799,23 @@ size_t job_bytes_estimate(const rbx_geometry &g, int nf)
 
 extern "C" {
 
+rbx_status rbx_pool_usage(size_t *used, size_t *reserved, int trim)
+{
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return RBX_ECUDA;
+    if (trim) {
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(pool, 0) != cudaSuccess) return RBX_ECUDA;
+    }
+    uint64_t u = 0, r = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess)
+        return RBX_ECUDA;
+    if (used) *used = (size_t)u;
+    if (reserved) *reserved = (size_t)r;
+    return RBX_OK;
+}
+
 rbx_status rbx_reconstruct(rbx_job *j, const double *freqs, int nf, const void *data_dev, rbx_stats *per_freq)
 {
     if (!j || !freqs || nf < 1 || !data_dev) return RBX_EINVAL;

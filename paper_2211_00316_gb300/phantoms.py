@@ -35,7 +35,7 @@ class Geometry:
     mask_frac: float = 0.9          # reconstruction mask radius / ring radius (Sec. 6.3)
     ds_frac: float = 0.5            # ray step / grid spacing
     weight_mode: int = 0            # 0 literal scattering-angle weight, 1 isochron weight
-    tau: float = 0.12               # step length (Sec. 6.3.2a)
+    tau: float = 0.12               # step length (Sec. 6.3.2a); sweeps set step_length(df)
 
     @property
     def x0(self) -> float:
@@ -81,6 +81,25 @@ class Workload:
     @property
     def dfreq(self) -> float:
         return float(self.freqs[1] - self.freqs[0]) if len(self.freqs) > 1 else 1.0e5
+
+
+# The paper's sweep: 180 frequencies over 0.2-1.72 MHz, two consecutive frequencies per
+# update, step length 0.12 (Sec. 6.3.2a). Its step per unit of frequency band is therefore
+# 0.12 over 2 x 8.49 kHz; a sweep of one frequency per update at spacing df takes the step
+# that moves the model as far per unit band.
+TAU_PAPER = 0.12
+DF_PAPER = (1.72e6 - 0.2e6) / 179.0
+FREQS_PER_SET_PAPER = 2
+
+
+def step_length(df: float) -> float:
+    """Step length of a one-frequency-per-update sweep at spacing df (Hz)."""
+    return TAU_PAPER * FREQS_PER_SET_PAPER * DF_PAPER / df
+
+
+def _with_step(w: "Workload") -> "Workload":
+    w.geom.tau = step_length(w.dfreq)
+    return w
 
 
 def _disc(X, Y, cx, cy, r):
@@ -171,7 +190,7 @@ def small_two_disc() -> Workload:
     """64-transducer ring at 45 mm, 96x96 grid at 1 mm, two discs, 200/300/400 kHz, 40 dB."""
     g = Geometry(nx=96, ny=96, dx=1e-3, n_xducers=64, ring_radius=45e-3)
     ct = two_disc_phantom(g)
-    return Workload("ring64_grid96_two_discs", g, np.array([2e5, 3e5, 4e5]), 40.0, ct, blur(ct, g.dx))
+    return _with_step(Workload("ring64_grid96_two_discs", g, np.array([2e5, 3e5, 4e5]), 40.0, ct, blur(ct, g.dx)))
 
 
 def breast(n_xducers: int, nx: int, dx: float, ring_radius: float, freqs, seed: int = 0,
@@ -179,7 +198,7 @@ def breast(n_xducers: int, nx: int, dx: float, ring_radius: float, freqs, seed: 
     g = Geometry(nx=nx, ny=nx, dx=dx, n_xducers=n_xducers, ring_radius=ring_radius)
     ct = breast_phantom(g, seed)
     nm = name or f"ring{n_xducers}_grid{nx}_breast_seed{seed}"
-    return Workload(nm, g, np.asarray(freqs, dtype=float), snr_db, ct, blur(ct, g.dx), {"seed": seed})
+    return _with_step(Workload(nm, g, np.asarray(freqs, dtype=float), snr_db, ct, blur(ct, g.dx), {"seed": seed}))
 
 
 def fp32_ring256() -> Workload:

@@ -81,6 +81,7 @@ _SIGS = {
     "rbx_server_poll": [_P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double), _P, C.POINTER(Stats)],
     "rbx_server_wait": [_P, C.c_longlong, C.c_double],
     "rbx_server_cancel": [_P, C.c_longlong],
+    "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
     "rbx_server_times": [_P, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "rbx_server_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
     "rbx_server_destroy": [_P],
@@ -91,6 +92,15 @@ _SIGS = {
 
 def exported_symbols() -> list[str]:
     return list(_SIGS) + ["rbx_last_error", "rbx_server_error", "rbx_estimate_bytes"]
+
+
+def pool_usage(trim: bool = False) -> dict:
+    """Bytes of the device's stream-ordered pool in live allocations and reserved (rbx_pool_usage)."""
+    u, r = C.c_size_t(), C.c_size_t()
+    st = load().rbx_pool_usage(C.byref(u), C.byref(r), int(trim))
+    if st != 0:
+        raise RbxError(st, "pool query failed")
+    return dict(used=u.value, reserved=r.value)
 
 
 def estimate_bytes(g, nf: int, precision: int = RBX_BF16) -> int:
