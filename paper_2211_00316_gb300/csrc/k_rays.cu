@@ -28,6 +28,16 @@ struct Fv {
     float n, gx, gy, hxx, hxy, hyy;
 };
 
+// 1/v for v in the range of a slowness or a triangle's edge sum: the hardware approximation
+// refined by one Newton-Raphson step, r <- r + r (1 - v r) (no special cases: v is finite
+// and away from 0 and the denormal range here).
+__device__ __forceinline__ float rcp_nr(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return fmaf(fmaf(-v, r, 1.f), r, r);
+}
+
 // s += inc with compensation term c (Kahan): the ray state is a sum of ~10^3 small steps
 __device__ __forceinline__ void kadd(float &s, float &c, float inc)
 {
@@ -94,34 +104,6 @@ __device__ __forceinline__ void cas_min_from(TabEntry *e, unsigned long long key
     atomicAdd(&counters[3], 1ull);
 }
 
-// One compare-and-swap in flight per lane. It is issued assuming the entry is untouched
-// (all ones, true for most nodes) and settled later: its result registers are first read
-// at the next flush, so the round trip overlaps the ray integration in between.
-struct PendingCas {
-    TabEntry *addr;
-    unsigned long long key, pay, lo, hi;
-    bool pend;
-};
-
-__device__ __forceinline__ void settle(PendingCas &q, unsigned long long *counters)
-{
-    if (!q.pend) return;
-    q.pend = false;
-    if (q.lo == ~0ull && q.hi == ~0ull) return;       // the entry was untouched: ours is stored
-    cas_min_from(q.addr, q.key, q.pay, q.lo, q.hi, counters);
-}
-
-__device__ __forceinline__ void issue(PendingCas &q, TabEntry *addr, unsigned long long key, unsigned long long pay,
-                                      unsigned long long *counters)
-{
-    settle(q, counters);
-    q.addr = addr;
-    q.key = key;
-    q.pay = pay;
-    cas128(reinterpret_cast<unsigned long long *>(addr), ~0ull, ~0ull, key, pay, q.lo, q.hi);
-    q.pend = true;
-}
-
 // Per-warp queue of table hits in shared memory, drained 32 at a time (one per lane):
 // node, key, and the interpolated amplitude and direction (the direction angle is formed
 // at the drain, where all 32 lanes are busy).
@@ -132,12 +114,16 @@ struct HitQueue {
     int n;       // warp-uniform
 };
 
-__device__ __forceinline__ void drain_one(const HitQueue &hq, int q, TabEntry *fan, PendingCas &pc,
-                                          unsigned long long *counters)
+__device__ __forceinline__ void drain_one(const HitQueue &hq, int q, TabEntry *fan, unsigned long long *counters)
 {
     const float4 v = hq.v[q];
+    const unsigned long long key = hq.key[q];
     const unsigned long long pay = ((unsigned long long)__float_as_uint(atan2f(v.z, v.y)) << 32) | __float_as_uint(v.x);
-    issue(pc, fan + hq.xi[q], hq.key[q], pay, counters);
+    TabEntry *addr = fan + hq.xi[q];
+    // most entries are still untouched (all ones): try that first, then take the minimum
+    unsigned long long lo, hi;
+    cas128(reinterpret_cast<unsigned long long *>(addr), ~0ull, ~0ull, key, pay, lo, hi);
+    if (!(lo == ~0ull && hi == ~0ull)) cas_min_from(addr, key, pay, lo, hi, counters);
 }
 
 // Edge function of P -> Q at (px, py), always evaluated from the vertex with the smaller
@@ -171,17 +157,18 @@ __device__ __forceinline__ unsigned long long tri_key(const Vtx &A, const Vtx &B
 // mask nodes of grid row iy: (first compact index, first ix, last ix).
 __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, const Vtx &P01, const Vtx &P10,
                                                  const Vtx &P11, uint32_t tid0, const RayParams &p, float inv_dx,
-                                                 const int4 *rows, TabEntry *fan, HitQueue &hq, PendingCas &pc,
+                                                 const int4 *rows, TabEntry *fan, HitQueue &hq,
                                                  unsigned long long *counters)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     bool ok0 = false, ok1 = false;
+    float ar0 = 0.f, ar1 = 0.f;
     int ix0 = 0, iy0 = 0, w = 0, cnt = 0;
     if (valid) {
         const float tiny = 1e-9f * p.ds * p.ds;
-        const float ar0 = (P10.x - P00.x) * (P11.y - P00.y) - (P10.y - P00.y) * (P11.x - P00.x);
-        const float ar1 = (P11.x - P00.x) * (P01.y - P00.y) - (P11.y - P00.y) * (P01.x - P00.x);
+        ar0 = (P10.x - P00.x) * (P11.y - P00.y) - (P10.y - P00.y) * (P11.x - P00.x);
+        ar1 = (P11.x - P00.x) * (P01.y - P00.y) - (P11.y - P00.y) * (P01.x - P00.x);
         ok0 = fabsf(ar0) > tiny;
         ok1 = fabsf(ar1) > tiny;
         if (ok0 || ok1) {
@@ -198,30 +185,43 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
             cnt = (w > 0 && h > 0) ? w * h : 0;
         }
     }
+    // A folded quad (its triangles of opposite orientation) can hold a node in both
+    // triangles; otherwise only the triangle on the node's side of the diagonal P00-P11 can.
+    const bool fold = ok0 && ok1 && ((ar0 > 0.f) != (ar1 > 0.f));
     int ix = ix0, iy = iy0;
     for (int it = 0; __any_sync(FULL, it < cnt); it++) {
-        bool hit = false;
+        bool act = false, hit = false;
         int xi = 0;
-        unsigned long long key = ~0ull;
-        float4 hv = make_float4(0.f, 0.f, 0.f, 0.f);
+        float px = 0.f, py = 0.f, e3 = 0.f;
         if (it < cnt) {
             const int4 ro = rows[iy];
             if (ix >= ro.y && ix <= ro.z) {
+                act = true;
                 xi = ro.x + ix - ro.y;
-                const float px = p.x0 + (float)ix * p.dx, py = p.y0 + (float)iy * p.dx;
+                px = p.x0 + (float)ix * p.dx;
+                py = p.y0 + (float)iy * p.dx;
+                e3 = edge_fn(P00, P11, px, py);
+            }
+            if (++ix >= ix0 + w) { ix = ix0; iy++; }
+        }
+        unsigned long long key = ~0ull;
+        float4 hv = make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool both = act && ok0 && ok1 && (fold || e3 == 0.f);
+        if (__any_sync(FULL, both)) {
+            // both triangles, the smaller key wins (nodes on the diagonal, folded quads)
+            if (act) {
                 const float e1 = edge_fn(P00, P10, px, py), e2 = edge_fn(P10, P11, px, py);
-                const float e3 = edge_fn(P00, P11, px, py), e4 = edge_fn(P01, P11, px, py);
-                const float e5 = edge_fn(P00, P01, px, py);
+                const float e4 = edge_fn(P01, P11, px, py), e5 = edge_fn(P00, P01, px, py);
                 float s0, s1, lb0 = 0.f, lc0 = 0.f, lb1 = 0.f, lc1 = 0.f;
                 unsigned long long k0 = ~0ull, k1 = ~0ull;
                 if (ok0 && tri_inside(e2, -e3, e1, s0)) {
-                    float inv = 1.f / s0;
+                    float inv = rcp_nr(s0);
                     lb0 = -e3 * inv;
                     lc0 = e1 * inv;
                     k0 = tri_key(P00, P10, P11, lb0, lc0, tid0);
                 }
                 if (ok1 && tri_inside(-e4, -e5, e3, s1)) {
-                    float inv = 1.f / s1;
+                    float inv = rcp_nr(s1);
                     lb1 = -e5 * inv;
                     lc1 = e3 * inv;
                     k1 = tri_key(P00, P11, P01, lb1, lc1, tid0 + 1);
@@ -238,7 +238,23 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
                     hit = true;
                 }
             }
-            if (++ix >= ix0 + w) { ix = ix0; iy++; }
+        } else if (act) {
+            // one triangle: t1 = (P00, P11, P01) where e3 has t1's orientation, else
+            // t0 = (P00, P10, P11). With M = P01 (t1) or P10 (t0) its other edges are M -> P11
+            // and P00 -> M, evaluated exactly as in the two-triangle path.
+            const bool use1 = ok1 && (!ok0 || ((e3 > 0.f) == (ar1 > 0.f)));
+            const Vtx &M = use1 ? P01 : P10;
+            const float x1 = edge_fn(M, P11, px, py), x2 = edge_fn(P00, M, px, py);
+            const float eBC = use1 ? -x1 : x1, eCA = use1 ? -x2 : -e3, eAB = use1 ? e3 : x2;
+            float s;
+            if (tri_inside(eBC, eCA, eAB, s)) {
+                const float inv = rcp_nr(s), lb = eCA * inv, lc = eAB * inv, la = 1.f - lb - lc;
+                const Vtx &B = use1 ? P11 : P10, &C = use1 ? P01 : P11;
+                key = tri_key(P00, B, C, lb, lc, tid0 + (use1 ? 1u : 0u));
+                hv = make_float4(la * P00.a + lb * B.a + lc * C.a, la * P00.kx + lb * B.kx + lc * C.kx,
+                                 la * P00.ky + lb * B.ky + lc * C.ky, 0.f);
+                hit = true;
+            }
         }
         const unsigned b = __ballot_sync(FULL, hit);
         if (b) {
@@ -251,7 +267,7 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
             hq.n += __popc(b);
             __syncwarp();
             if (hq.n >= 32) {
-                drain_one(hq, hq.n - 32 + lane, fan, pc, counters);
+                drain_one(hq, hq.n - 32 + lane, fan, counters);
                 hq.n -= 32;
                 __syncwarp();
             }
@@ -281,8 +297,6 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
     TabEntry *fan = tab + (size_t)e * p.X;
     const float ds = p.ds, hds = 0.5f * p.ds, inv_dx = p.inv_dx, R2 = p.R * p.R;
     HitQueue hq{q_xi[wib], q_key[wib], q_v[wib], 0};
-    PendingCas pc{};
-    pc.pend = false;
 
     const double be = 2.0 * 3.14159265358979323846 * e / N;
     float x = (float)(p.R * cos(be)), y = (float)(p.R * sin(be));
@@ -310,7 +324,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
         bool have = false;
         if (alive) {
             // stage 1 at x: normalise p to n(x), q_x = p/n, q_p = grad n
-            const float n = F1.n, in = 1.f / n;
+            const float n = F1.n, in = rcp_nr(n);
             const float sc = n * rsqrtf(px * px + py * py);
             px *= sc; py *= sc;
             cpx *= sc; cpy *= sc;
@@ -318,7 +332,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             // stage 2 at the auxiliary point x + ds q_x
             Fv F2;
             field_eval(F, p, x + ds * qx, y + ds * qy, F2);
-            const float na = F2.n, ina = 1.f / na;
+            const float na = F2.n, ina = rcp_nr(na);
             float pax = px + ds * F1.gx, pay = py + ds * F1.gy;
             const float sca = na * rsqrtf(pax * pax + pay * pay);
             pax *= sca; pay *= sca;
@@ -394,15 +408,14 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
         const bool nhave = __shfl_down_sync(FULL, (int)have, 1) != 0;
         const bool valid = i >= 1 && have && nhave && lane < 31 && j + 1 <= N - 1;
         raster_quad_warp(valid, prev, cur, nprev, ncur, ((uint32_t)j << 11 | (uint32_t)i) << 1, p, inv_dx, rows, fan,
-                         hq, pc, counters);
+                         hq, counters);
         prev = cur;
         nprev = ncur;
         if (!__any_sync(FULL, alive)) break;
         if (i == p.maxs - 1 && alive) atomicAdd(&counters[2], 1ull);   // ray never reached the ring
     }
-    // drain the queue and settle every exchange still in flight
-    if (lane < hq.n) drain_one(hq, lane, fan, pc, counters);
-    settle(pc, counters);
+    // drain the rest of the queue
+    if (lane < hq.n) drain_one(hq, lane, fan, counters);
 }
 
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
