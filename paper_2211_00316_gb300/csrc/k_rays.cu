@@ -308,12 +308,30 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
     float px, py, dpx, dpy, dxx = 0.f, dxy = 0.f, T = 0.f, Tc = 0.f;
     // compensation terms of x, p, dx (T has Tc)
     float cx = 0.f, cy = 0.f, cpx = 0.f, cpy = 0.f, cdx = 0.f, cdy = 0.f;
+
+    // Uniform water near the ring (exact up to rounding). Beyond radius rho every cell that a
+    // sample or an auxiliary point can touch holds the same medium with zero derivatives (rho
+    // exceeds the largest radius of a non-uniform node by a cell diagonal and a step), so there
+    // a ray is a straight line with constant n and a linearly growing paraxial deviation; rho
+    // also stays two cells outside the mask, so a quad with all vertices beyond rho holds no
+    // mask node. Up to its entry step kin (its last sample beyond rho on the way in) a ray
+    // takes the closed form of the step; kin depends on the ray alone, so the ray shared by two
+    // warps has identical samples in both. The warp rasterises nothing before its smallest kin.
+    const float ru = __uint_as_float((unsigned)counters[7]);
+    const float rho = fmaxf(ru + 1.5f * p.dx + ds, p.rmask + 2.f * p.dx), rho2 = rho * rho;
+    int kin = 0;
     {
         float s0, c0;
         sincosf(gam0, &s0, &c0);
         px = F1.n * c0; py = F1.n * s0;
         dpx = -F1.n * s0; dpy = F1.n * c0;
+        if (has_ray && R2 > rho2) {
+            const float b = x * c0 + y * s0, disc = b * b - (fmaf(x, x, y * y) - rho2);
+            const float s_in = disc >= 0.f ? -b - sqrtf(disc) : -b;   // entry, or closest approach
+            kin = max(0, (int)floorf(s_in / ds) - 1);
+        }
     }
+    const int i0 = __reduce_min_sync(FULL, has_ray ? kin : 0x7fffffff);
     float sc1 = 0.f, Jlast = 0.f;   // sc1 = sqrt(n_1 |J_1| / ds): a_i = sc1 / sqrt(n_i |J_i|)
     int K = 0;
     bool alive = has_ray;
@@ -322,7 +340,21 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
     for (int i = 0; i < p.maxs; i++) {
         Vtx cur{};
         bool have = false;
-        if (alive) {
+        if (alive && i < kin) {
+            // the step below in a uniform medium: straight, p constant, dx += ds dp / n
+            const float n = F1.n, in = rcp_nr(n);
+            const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
+            kadd(x, cx, ds * tx); kadd(y, cy, ds * ty);
+            kadd(dxx, cdx, ds * (dpx * in)); kadd(dxy, cdy, ds * (dpy * in));
+            kadd(T, Tc, hds * (n + n));
+            const float J = dxx * ty - dxy * tx;
+            if (i == 0) { sc1 = sqrtf(n * fabsf(J) / ds); Jlast = J; }
+            else if (J * Jlast < 0.f) K++;
+            if (J != 0.f) Jlast = J;
+            cur.x = x; cur.y = y; cur.T = T; cur.kx = tx; cur.ky = ty; cur.K = K;
+            cur.a = sc1 * rsqrtf(n * fabsf(J));
+            have = true;
+        } else if (alive) {
             // stage 1 at x: normalise p to n(x), q_x = p/n, q_p = grad n
             const float n = F1.n, in = rcp_nr(n);
             const float sc = n * rsqrtf(px * px + py * py);
@@ -406,16 +438,81 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
         ncur.ky = __shfl_down_sync(FULL, cur.ky, 1);
         ncur.K = __shfl_down_sync(FULL, cur.K, 1);
         const bool nhave = __shfl_down_sync(FULL, (int)have, 1) != 0;
-        const bool valid = i >= 1 && have && nhave && lane < 31 && j + 1 <= N - 1;
+        const bool valid = i >= 1 && i >= i0 && have && nhave && lane < 31 && j + 1 <= N - 1;
         raster_quad_warp(valid, prev, cur, nprev, ncur, ((uint32_t)j << 11 | (uint32_t)i) << 1, p, inv_dx, rows, fan,
                          hq, counters);
         prev = cur;
         nprev = ncur;
+        // Leaving through the uniform water: once a ray is beyond rho, moving outward, and so
+        // are (or have ended) the rays it forms quads with in this warp, no later quad of it
+        // can hold a mask node, and it goes straight to the ring in closed form (the chord's
+        // crossing as in the last step above; J is linear in s there, so at most one caustic).
+        {
+            const bool out = alive && i >= kin && fmaf(x, x, y * y) > rho2 && fmaf(x, px, y * py) > 0.f;
+            if (__any_sync(FULL, out)) {
+                const bool okself = !alive || out;
+                bool okL = __shfl_up_sync(FULL, okself, 1), okR = __shfl_down_sync(FULL, okself, 1);
+                const bool aL = __shfl_up_sync(FULL, alive, 1), aR = __shfl_down_sync(FULL, alive, 1);
+                const float xl = __shfl_up_sync(FULL, x, 1), yl = __shfl_up_sync(FULL, y, 1);
+                const float xr = __shfl_down_sync(FULL, x, 1), yr = __shfl_down_sync(FULL, y, 1);
+                const float gap = rho - p.rmask, gap2 = gap * gap;
+                if (lane == 0) okL = true;
+                else if (aL) okL = okL && (x - xl) * (x - xl) + (y - yl) * (y - yl) < gap2;
+                if (lane == 31) okR = true;
+                else if (aR) okR = okR && (x - xr) * (x - xr) + (y - yr) * (y - yr) < gap2;
+                if (out && okL && okR) {
+                    const float n = F1.n, in = rcp_nr(n), inc = hds * (n + n);
+                    const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
+                    const float b = x * tx + y * ty, se = -b + sqrtf(fmaxf(b * b - (fmaf(x, x, y * y) - R2), 0.f));
+                    const int m = max(0, (int)floorf(se / ds));
+                    const float sm = (float)m * ds;
+                    const float xm = fmaf(sm, tx, x), ym = fmaf(sm, ty, y);
+                    const float b2 = xm * tx + ym * ty, disc = b2 * b2 - (fmaf(xm, xm, ym * ym) - R2);
+                    float t = -b2 + sqrtf(disc > 0.f ? disc : 0.f);
+                    t = fminf(fmaxf(t, 0.f), ds);
+                    x = fmaf(t, tx, xm); y = fmaf(t, ty, ym);
+                    kadd(T, Tc, (float)m * inc);
+                    kadd(T, Tc, (t / ds) * inc);
+                    dxx = fmaf(sm + t, dpx * in, dxx); dxy = fmaf(sm + t, dpy * in, dxy);
+                    field_eval(F, p, x, y, F1);
+                    const float J = dxx * ty - dxy * tx;
+                    if (J * Jlast < 0.f) K++;
+                    const float a = sc1 * rsqrtf(F1.n * fabsf(J));
+                    if (lane < 31 || j == N - 1)
+                        exits[(size_t)e * (N - 1) + (j - 1)] = make_float4(atan2f(y, x), T, a, (float)K);
+                    alive = false;
+                }
+            }
+        }
         if (!__any_sync(FULL, alive)) break;
         if (i == p.maxs - 1 && alive) atomicAdd(&counters[2], 1ull);   // ray never reached the ring
     }
     // drain the rest of the queue
     if (lane < hq.n) drain_one(hq, lane, fan, counters);
+}
+
+// Largest radius of a node whose fields differ from the uniform medium of node (0, 0)
+// (n there, all derivatives zero); +inf when node (0, 0) itself is not uniform.
+__global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsigned long long *ru)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.nx * p.ny) return;
+    const float4 u0 = F[0], u1 = F[1], a0 = F[2 * (size_t)k], a1 = F[2 * (size_t)k + 1];
+    if (k == 0 && !(u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && u1.x == 0.f && u1.y == 0.f)) {
+        atomicMax(ru, (unsigned long long)__float_as_uint(__int_as_float(0x7f800000)));
+        return;
+    }
+    const bool uni = a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f;
+    if (!uni) {
+        const float px = p.x0 + (float)(k % p.nx) * p.dx, py = p.y0 + (float)(k / p.nx) * p.dx;
+        atomicMax(ru, (unsigned long long)__float_as_uint(sqrtf(px * px + py * py)));
+    }
+}
+
+void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s)
+{
+    const int n = p.nx * p.ny;
+    k_uniform_radius<<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float4 *>(fields), p, ru);
 }
 
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,

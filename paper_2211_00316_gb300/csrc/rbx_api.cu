@@ -321,9 +321,12 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     p.N = w.N; p.X = w.X; p.nx = w.nx; p.ny = w.ny;
     p.dx = (float)j->g.dx; p.x0 = (float)j->g.x0; p.y0 = (float)j->g.y0;
     p.R = (float)j->g.ring_radius; p.ds = (float)j->g.ds; p.inv_dx = (float)(1.0 / j->g.dx);
+    p.rmask = (float)j->g.mask_radius;
     p.maxs = max_steps(j->g);
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
+    launch_uniform_radius(w.fields, p, w.counters + 7, j->stream);
     launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->stream);
-    LAUNCHED(j, 1);
+    LAUNCHED(j, 2);
     if ((st = record(j, EV_TRACE))) return st;
     launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
     LAUNCHED(j, 1);

@@ -27,7 +27,7 @@ struct __align__(16) TabEntry {
 
 struct RayParams {
     int N, X, nx, ny;
-    float dx, x0, y0, R, ds, inv_dx;
+    float dx, x0, y0, R, ds, inv_dx, rmask;
     int maxs;
 };
 
@@ -63,7 +63,7 @@ struct Workspace {
     float2 *data = nullptr;
     double *red = nullptr;           // reduction scratch
     double *hist = nullptr;          // [kHistSlots][kHistStride] per-update scalars
-    unsigned long long *counters = nullptr;   // [0] uncovered [1] clamped [2] bad rays [3] CAS bound [4] m <= 0 [5] bad model [6] mask count
+    unsigned long long *counters = nullptr;   // [0] uncovered [1] clamped [2] bad rays [3] CAS bound [4] m <= 0 [5] bad model [6] mask count [7] uniform radius (float bits)
     int fwd_splits = 1;
     TcPlanes tc;
 };
@@ -78,6 +78,7 @@ void launch_check_model(const float *c, int n, unsigned long long *flag, cudaStr
 void launch_fill(float *p, float v, size_t n, cudaStream_t s);
 
 // k_rays.cu
+void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s);
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
                          unsigned long long *counters, cudaStream_t s);
 void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s);
