@@ -69,10 +69,21 @@ def peaks():
             "source": "measured" if p else "fallback"}
 
 
-def kernel_src_hash() -> str:
+# source files that define each timed kernel (a recorded ncu traffic figure is valid only for
+# the sources it was taken on)
+KERNEL_SRC = {
+    "trace": ["k_rays.cu"],
+    "gemm_fwd": ["k_gemm_tc.cu", "tc_sm100.cuh", "k_gemm_simt.cu"],
+    "gemm_bp": ["k_gemm_tc.cu", "tc_sm100.cuh", "k_gemm_simt.cu"],
+    "synth_fwd": ["k_gemm_tc.cu", "k_gemm_simt.cu"],
+    "synth_bp": ["k_gemm_tc.cu", "k_gemm_simt.cu"],
+}
+
+
+def kernel_src_hash(kernel: str) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2211_00316_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SRC.get(kernel, sorted(os.listdir(d))):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -81,8 +92,9 @@ def kernel_src_hash() -> str:
 # DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (workload, kernel); valid only for the kernel sources they were taken on.
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_trace_raster -s 2 -c 1 (1 pass)
-    ("precision_ring1024", "trace"): {"bytes": 2.52e9 + 2.48e9, "src": "c14d9d3759c8"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:k_trace_raster
+    #     -s 2 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --serve-requests 0 (1 pass)
+    ("precision_ring1024", "trace"): {"bytes": 2.518852864e9 + 2.458076160e9, "src": "4405b6ae7d56"},
 }
 
 
@@ -536,14 +548,17 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    # per-kernel device time averaged over the timed steps; roofline of the dominant kernel
+    # per-kernel device time averaged over the timed steps; roofline of every kernel with an
+    # algorithmic work figure, and of the dominant one
     kms = {k: float(np.mean([s["ms_kernel"][k] for s in stats])) for k in stats[0]["ms_kernel"]}
     dom = max(kms, key=kms.get)
     pk = peaks()
-    amount, unit, bound = algorithmic(dom, N, X, args.precision)
-    roof = None
-    if amount is not None:
-        dur = kms[dom] / 1e3
+
+    def roofline(kernel):
+        amount, unit, bound = algorithmic(kernel, N, X, args.precision)
+        if amount is None or kms.get(kernel, 0.0) <= 0.0:
+            return None
+        dur = kms[kernel] / 1e3
         if bound == "hbm":
             achieved, peak, u = amount / dur / 1e9, pk["hbm_gbs"], "GB/s"
         elif bound == "tensor":
@@ -552,12 +567,15 @@ def main():
             achieved = amount / dur / 1e12
             peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
             u = "TFLOP/s"
-        tr = NCU_TRAFFIC.get((args.workload, dom))
-        traffic = tr["bytes"] if tr and tr.get("src") == kernel_src_hash() else None
-        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
-                "frac": achieved / peak, "traffic": traffic, "algorithmic_per_launch": amount,
-                "peak_source": (pk["source"] if bound != "alu" else
-                                "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2070 MHz")}
+        tr = NCU_TRAFFIC.get((args.workload, kernel))
+        traffic = tr["bytes"] if tr and tr.get("src") == kernel_src_hash(kernel) else None
+        return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
+                "frac": achieved / peak, "traffic": traffic, "algorithmic_per_launch": amount, "ms": kms[kernel],
+                "peak_source": ((pk["source"] + (" sustained bf16" if bound == "tensor" else " copy bandwidth"))
+                                if bound != "alu" else "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2070 MHz")}
+
+    roof = roofline(dom)
+    roofs = [r for r in (roofline(k) for k in sorted(kms, key=kms.get, reverse=True)) if r is not None]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
@@ -566,7 +584,7 @@ def main():
                        "l2": "inputs larger than L2 (tables N*X*16 B = %.2f GB)" % (16.0 * N * X / 1e9),
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": int(sum(s["n_launches"] for s in stats)),
-            "clocks": clk, "e2e": e2e, "roofline": roof,
+            "clocks": clk, "e2e": e2e, "roofline": roof, "rooflines": roofs,
             "kernel_ms": kms, "stage_ms": {k: float(np.mean([s[k] for s in stats]))
                                            for k in ("ms_trace", "ms_forward", "ms_backproj", "ms_total")},
             "n_uncovered": int(stats[-1]["n_uncovered"]), "rms_dc_last": stats[-1]["rms_dc"]}

@@ -271,6 +271,20 @@ rbx_status rbx_server_destroy(rbx_server *srv);
 /* Last error message of the job ("" if none). The string lives as long as the job. */
 const char *rbx_last_error(const rbx_job *job);
 
+/* Autotuning of the BF16 forward contraction's K split (split across CTAs of each upper
+ * tile pair, partial sums reduced in a fixed order). mode 1 (default): the first job of a
+ * given (device, N, mask size, precision) in the process times up to five split counts on
+ * its own operand planes inside rbx_set_geometry and keeps the fastest; later jobs of that
+ * shape reuse it, so results within a process are reproducible. mode 0: the fixed
+ * heuristic (about one CTA per SM), reproducible across processes. Other values only
+ * query. Returns the previous mode. The choice changes the forward's summation order, so
+ * results differ between split counts by rounding (within the BF16 tolerance). */
+int rbx_autotune(int mode);
+
+/* The forward K split the job uses and the number of candidates it timed (0: reused or
+ * heuristic). */
+rbx_status rbx_get_tuning(const rbx_job *job, int *fwd_splits, int *candidates_timed);
+
 /* Device memory of the stream-ordered pool all jobs of the current device allocate from:
  * bytes held by live allocations (used) and bytes the pool has taken from the device
  * (reserved; freed workspaces stay reserved for reuse). trim != 0 first returns the unused

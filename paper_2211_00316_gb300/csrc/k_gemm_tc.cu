@@ -21,7 +21,12 @@
 #include "tc_sm100.cuh"
 
 #include <cuda_bf16.h>
+
+#include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 namespace rbx {
 using namespace tc;
@@ -523,6 +528,9 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t st)
     int kper = (nk + splits - 1) / splits;
     p.fwd_kper = kper;
     p.fwd_splits = (nk + kper - 1) / kper;
+    // the autotuner may go up to 4x the heuristic's split (at most one K chunk per CTA)
+    const int smax = std::min(nk, std::max(4 * splits, 1));
+    p.fwd_max_splits = (nk + (nk + smax - 1) / smax - 1) / ((nk + smax - 1) / smax);
     const size_t fbytes = mult * 4 * p.fwd_pstride * sizeof(__nv_bfloat16);
     const size_t bbytes = mult * 6 * p.bp_pstride * sizeof(__nv_bfloat16);
     const size_t rbytes = mult * 2 * (size_t)p.Npad * p.Npad * sizeof(__nv_bfloat16);
@@ -561,6 +569,91 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t st)
     return ok;
 }
 
+// ---------------------------------------------------------------- autotuning
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, bool>, int> g_tune;   // (device, N, X, split) -> K chunks per CTA
+int g_tune_mode = 1;
+}  // namespace
+
+int set_autotune(int mode)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int old = g_tune_mode;
+    if (mode == 0 || mode == 1) g_tune_mode = mode;
+    return old;
+}
+
+static void apply_kper(TcPlanes &p, int kper)
+{
+    const int nk = p.Xpad / BK;
+    p.fwd_kper = kper;
+    p.fwd_splits = (nk + kper - 1) / kper;
+}
+
+bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, p.N, p.X, p.split);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune_mode == 0) return true;                      // heuristic split
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            apply_kper(p, it->second);
+            return true;
+        }
+    }
+    const int nk = p.Xpad / BK, T = p.Npad / BM, pairs = T * (T + 1) / 2;
+    const int base = p.fwd_splits;
+    std::vector<int> kpers;
+    for (int m : {1, 2, 3, 4, -2}) {                             // -2: half the split
+        int sp = m > 0 ? base * m : std::max(1, base / 2);
+        sp = std::min(sp, p.fwd_max_splits);
+        const int kper = (nk + sp - 1) / sp;
+        if (std::find(kpers.begin(), kpers.end(), kper) == kpers.end()) kpers.push_back(kper);
+    }
+    Maps4 hi{p.fmaps[0][0], p.fmaps[0][1], p.fmaps[0][2], p.fmaps[0][3]};
+    Maps4 lo{p.fmaps[1][0], p.fmaps[1][1], p.fmaps[1][2], p.fmaps[1][3]};
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return false;
+    int best = p.fwd_kper;
+    float best_ms = 1e30f;
+    bool ok = true;
+    for (int kper : kpers) {
+        const int sp = (nk + kper - 1) / kper;
+        float tot = 0.f;
+        for (int rep = 0; rep < 3 && ok; rep++) {              // first launch warms up
+            ok = cudaEventRecord(a, s) == cudaSuccess;
+            k_forward_tc<<<dim3(pairs, sp), 192, F_SMEM, s>>>(hi, lo, p.split ? 3 : 1, p.N, T, nk, kper, part, p.err);
+            ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(b, s) == cudaSuccess &&
+                 cudaEventSynchronize(b) == cudaSuccess;
+            float ms = 0.f;
+            ok = ok && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+            if (rep > 0) tot += ms;
+        }
+        if (!ok) break;
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = kper;
+        }
+        p.tuned++;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!ok) return false;
+    unsigned zero = 0;
+    if (cudaMemcpyAsync(p.err, &zero, sizeof zero, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return false;
+    apply_kper(p, best);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.emplace(key, best);
+    return true;
+}
+
 void tc_free(TcPlanes &p, cudaStream_t st)
 {
     void *ps[] = {p.fplanes, p.bplanes, p.rsplanes, p.bpart, p.err};
@@ -574,14 +667,17 @@ static float green_const_tc(double f, double c0)
     return (float)(1.0 / sqrt(8.0 * 3.14159265358979323846 * (2.0 * 3.14159265358979323846 * f) / c0));
 }
 
-int launch_forward_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, float2 *part,
-                      cudaStream_t s)
+void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, cudaStream_t s)
 {
     size_t n = (size_t)p.N * p.X;
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     k_synth_fwd_tc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, v, p.N, p.X, p.Xpad, p.fwd_pstride, fhi, flo,
                                                                green_const_tc(f, c0),
                                                                static_cast<__nv_bfloat16 *>(p.fplanes), p.split);
+}
+
+int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s)
+{
     int T = p.Npad / BM, pairs = T * (T + 1) / 2;
     Maps4 hi{p.fmaps[0][0], p.fmaps[0][1], p.fmaps[0][2], p.fmaps[0][3]};
     Maps4 lo{p.fmaps[1][0], p.fmaps[1][1], p.fmaps[1][2], p.fmaps[1][3]};

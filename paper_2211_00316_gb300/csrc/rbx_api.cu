@@ -235,9 +235,14 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
             free_ws(w, j->stream);
             return fail(j, RBX_ENOMEM, "tensor-core operand set-up failed (allocation or TMA descriptor)");
         }
-        if (w.tc.fwd_splits > w.fwd_splits) w.fwd_splits = w.tc.fwd_splits;
+        if (w.tc.fwd_max_splits > w.fwd_splits) w.fwd_splits = w.tc.fwd_max_splits;
     }
     ALLOC(w.part, (size_t)w.fwd_splits * N * N);
+    if (g.precision != RBX_FP32 && !tc_autotune(w.tc, w.part, j->stream)) {
+        cudaGetLastError();
+        free_ws(w, j->stream);
+        return fail(j, RBX_ECUDA, "autotuning of the tensor-core forward failed");
+    }
     ALLOC(w.gpart, 2 * (size_t)X);
     // residual partials + total, then the update's partials + totals (disjoint regions)
     ALLOC(w.red, (size_t)residual_blocks(w.N) + 8 + 3 * (size_t)update_blocks(g.nx, g.ny) + 8);
@@ -385,11 +390,12 @@ static rbx_status forward_core(rbx_job *j, double f, bool timed)
     Workspace &w = j->w;
     rbx_status st;
     if (j->g.precision != RBX_FP32) {
-        // the BF16 operand synthesis is fused into the first launch of launch_forward_tc
+        launch_synth_fwd_tc(w.tc, w.tab, w.v, f, j->g.c0, j->stream);
+        LAUNCHED(j, 1);
         if (timed && (st = record(j, EV_SYNTH_F))) return st;
-        int splits = launch_forward_tc(w.tc, w.tab, w.v, f, j->g.c0, w.part, j->stream);
+        int splits = launch_forward_tc(w.tc, w.part, j->stream);
         launch_forward_reduce(w.part, w.N, splits, w.D, j->stream);
-        LAUNCHED(j, 3);
+        LAUNCHED(j, 2);
     } else {
         launch_synth_fwd(w.tab, w.N, w.X, f, j->g.c0, w.G, j->stream);
         LAUNCHED(j, 1);
@@ -801,6 +807,16 @@ size_t job_bytes_estimate(const rbx_geometry &g, int nf)
 }  // namespace rbx
 
 extern "C" {
+
+int rbx_autotune(int mode) { return set_autotune(mode); }
+
+rbx_status rbx_get_tuning(const rbx_job *j, int *fwd_splits, int *candidates_timed)
+{
+    if (!j) return RBX_EINVAL;
+    if (fwd_splits) *fwd_splits = j->g.precision == RBX_FP32 ? j->w.fwd_splits : j->w.tc.fwd_splits;
+    if (candidates_timed) *candidates_timed = j->w.tc.tuned;
+    return RBX_OK;
+}
 
 rbx_status rbx_pool_usage(size_t *used, size_t *reserved, int trim)
 {

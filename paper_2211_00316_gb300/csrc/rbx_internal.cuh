@@ -37,6 +37,8 @@ struct TcPlanes {
     int N = 0, X = 0, Npad = 0, Xpad = 0, Xp = 0, sms = 0;
     size_t fwd_pstride = 0, bp_pstride = 0;
     int fwd_splits = 1, fwd_kper = 1;
+    int fwd_max_splits = 1;    // largest K split the autotuner may pick (sizes the partials)
+    int tuned = 0;             // candidates timed for this job (0: heuristic or cached choice)
     bool split = false;        // split BF16: every plane set is followed by its lo set
     void *fplanes = nullptr;   // [4][Npad][Xpad] bf16: Gre, Gim, (Gv)re, (Gv)im
     void *bplanes = nullptr;   // [6][Xp][Npad] bf16: u, conj(kappa) u, kappa u (re, im)
@@ -105,9 +107,13 @@ void launch_backproject_simt(const float2 *A, const float2 *kap, const float2 *R
 
 // k_gemm_tc.cu (BF16 tensor cores)
 bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t s);
+// Choose the forward K split by timing the candidates on this job's planes (once per shape
+// and process; later jobs of the shape reuse the choice). part holds fwd_max_splits partials.
+bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s);
+int set_autotune(int mode);
 void tc_free(TcPlanes &p, cudaStream_t s);
-int launch_forward_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, float2 *part,
-                      cudaStream_t s);
+void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, cudaStream_t s);
+int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s);
 void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, double f, double c0, cudaStream_t s);
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s);
 

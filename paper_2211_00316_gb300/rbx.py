@@ -81,6 +81,7 @@ _SIGS = {
     "rbx_server_poll": [_P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double), _P, C.POINTER(Stats)],
     "rbx_server_wait": [_P, C.c_longlong, C.c_double],
     "rbx_server_cancel": [_P, C.c_longlong],
+    "rbx_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
     "rbx_server_times": [_P, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "rbx_server_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
@@ -91,7 +92,12 @@ _SIGS = {
 
 
 def exported_symbols() -> list[str]:
-    return list(_SIGS) + ["rbx_last_error", "rbx_server_error", "rbx_estimate_bytes"]
+    return list(_SIGS) + ["rbx_last_error", "rbx_server_error", "rbx_estimate_bytes", "rbx_autotune"]
+
+
+def autotune(mode: int = -1) -> int:
+    """Set (0 heuristic, 1 autotune) or query (-1) the forward split autotuning; returns the previous mode."""
+    return int(load().rbx_autotune(int(mode)))
 
 
 def pool_usage(trim: bool = False) -> dict:
@@ -126,6 +132,8 @@ def load(path: str | None = None):
             L.rbx_last_error.restype = C.c_char_p
             L.rbx_server_error.argtypes = [_P, C.c_longlong]
             L.rbx_server_error.restype = C.c_char_p
+            L.rbx_autotune.argtypes = [C.c_int]
+            L.rbx_autotune.restype = C.c_int
             L.rbx_estimate_bytes.argtypes = [C.POINTER(Geometry), C.c_int]
             L.rbx_estimate_bytes.restype = C.c_size_t
             _lib = L
@@ -267,6 +275,11 @@ class Job:
         st = Stats()
         self._check(self.L.rbx_get_stats(self.h, slot, C.byref(st)))
         return st.as_dict()
+
+    def tuning(self) -> dict:
+        sp, nc = C.c_int(), C.c_int()
+        self._check(self.L.rbx_get_tuning(self.h, C.byref(sp), C.byref(nc)))
+        return dict(fwd_splits=sp.value, candidates_timed=nc.value)
 
     def sync(self):
         self._check(self.L.rbx_synchronize(self.h))

@@ -122,3 +122,29 @@ def test_bf16_and_fp32_paths_agree(case):
     assert np.sqrt(np.mean(d ** 2)) <= 0.01 * scale
     d3 = out[rbx.RBX_BF16X3][m] - out[rbx.RBX_FP32][m]
     assert np.sqrt(np.mean(d3 ** 2)) <= 1e-3 * scale
+
+
+def test_forward_split_autotuning():
+    """The first job of a shape times the candidate K splits and keeps one; later jobs of the
+    shape reuse it; the fixed heuristic gives the same forward within the BF16 rounding."""
+    w = P.custom(72, 96, 0.9e-3, 38e-3, kind="discs", freqs=(3e5,))
+    c = dev(w.c_init.astype(np.float32))
+    prev = rbx.autotune(1)
+    try:
+        outs, tunings = [], []
+        for mode in (1, 1, 0):
+            rbx.autotune(mode)
+            j = rbx.Job()
+            j.set_geometry(w.geom, precision=rbx.RBX_BF16)
+            j.set_model(c)
+            j.trace_rays(3e5)
+            dm = torch.full((w.geom.ny, w.geom.nx), 1e-9, device="cuda")
+            outs.append(j.forward(3e5, dm).cpu().numpy())
+            tunings.append(j.tuning())
+            j.close()
+        assert tunings[0]["candidates_timed"] >= 2 and tunings[1]["candidates_timed"] == 0
+        assert tunings[0]["fwd_splits"] == tunings[1]["fwd_splits"] >= 1
+        np.testing.assert_array_equal(outs[0], outs[1])
+        assert rel_l2(outs[2], outs[0]) <= 1e-5
+    finally:
+        rbx.autotune(prev)
