@@ -53,7 +53,7 @@ class OGeom(C.Structure):
 class OMedium(C.Structure):
     _fields_ = [("mode", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("x0", C.c_double),
                 ("y0", C.c_double), ("f", C.POINTER(C.c_double)), ("c1", C.c_double), ("gx", C.c_double),
-                ("gy", C.c_double)]
+                ("gy", C.c_double), ("al", C.POINTER(C.c_double))]
 
 
 _D = C.POINTER(C.c_double)
@@ -84,6 +84,18 @@ def _declare(L):
     L.og_update_frequency.argtypes = [_G, C.c_double, C.c_double, _D, _D, _D, _D]
     L.og_update_frequency.restype = C.c_int
     L.og_num_threads.argtypes = []; L.og_num_threads.restype = C.c_int
+    L.og_smooth_abs.argtypes = [_G, _D, _D, C.c_double, C.c_double, C.c_int, _D, _D, _D]
+    L.og_smooth_abs.restype = None
+    L.og_tables_abs.argtypes = [_G, _D, _D, _I, C.c_int, _D, _D, _D, _I, _I, _D, C.POINTER(C.c_long)]
+    L.og_tables_abs.restype = C.c_long
+    L.og_forward_c.argtypes = [_G, C.c_double, C.c_int, _D, _D, _I, _D, _D]; L.og_forward_c.restype = None
+    L.og_adjoint_plain_c.argtypes = [_G, C.c_double, C.c_int, _D, _D, _I, _D, _D, _I, C.c_int, _D]
+    L.og_adjoint_plain_c.restype = None
+    L.og_update_abs.argtypes = [_G, C.c_double, C.c_double, C.c_int, _I, _D, _D, _D, C.c_double, _D, _D]
+    L.og_update_abs.restype = C.c_int
+    L.og_predict_abs.argtypes = [_G, C.c_double, _D, _D, C.c_double, _D, _D]; L.og_predict_abs.restype = None
+    L.og_update_frequency_abs.argtypes = [_G, C.c_double, C.c_double, _D, _D, C.c_double, _D, _D, _D]
+    L.og_update_frequency_abs.restype = C.c_int
 
 
 def _d(a):
@@ -154,27 +166,49 @@ class Oracle:
         ns = self.smooth(c, self.window(f))
         return ns, self.fields(ns)
 
+    def smooth_abs(self, c, alpha0, y: float, f: float, w: int | None = None):
+        """Smoothed 1/c, ray slowness n_e and absorption coefficient alpha (Np/m)."""
+        c, a0 = _f64(c), _f64(alpha0)
+        ns, ne, al = np.zeros_like(c), np.zeros_like(c), np.zeros_like(c)
+        self.L.og_smooth_abs(C.byref(self.g), _d(c), _d(a0), y, f, self.window(f) if w is None else w, _d(ns),
+                             _d(ne), _d(al))
+        return ns, ne, al
+
+    def fields_for_abs(self, c, alpha0, y: float, f: float):
+        """(ns, fields of n_e, alpha): the lossy counterpart of fields_for."""
+        ns, ne, al = self.smooth_abs(c, alpha0, y, f)
+        return ns, self.fields(ne), al
+
     # a2
-    def trace_ray(self, xs, ys, gam0, f6=None, linear=None, maxs=None, R=None, ds=None):
-        """Samples of one ray: columns x, y, T, J, a, gamma, K, n, dH, px, py, s."""
+    def trace_ray(self, xs, ys, gam0, f6=None, linear=None, maxs=None, R=None, ds=None, al=None):
+        """Samples of one ray: columns x, y, T, J, a, gamma, K, n, dH, px, py, s, B (al: alpha map)."""
         g = self.geom
         maxs = maxs or int(np.ceil(3 * g.ring_radius / (ds or g.ds))) + 8
         if linear is not None:
             c1, gx, gy = linear
-            med = OMedium(1, g.nx, g.ny, g.dx, g.x0, g.y0, None, c1, gx, gy)
+            med = OMedium(1, g.nx, g.ny, g.dx, g.x0, g.y0, None, c1, gx, gy, None)
         else:
             f6 = _f64(f6)
-            med = OMedium(0, g.nx, g.ny, g.dx, g.x0, g.y0, _d(f6), 0.0, 0.0, 0.0)
-        rows = np.zeros((maxs + 1, 12))
+            alp = None
+            if al is not None:
+                al = _f64(al)
+                alp = _d(al)
+            med = OMedium(0, g.nx, g.ny, g.dx, g.x0, g.y0, _d(f6), 0.0, 0.0, 0.0, alp)
+        rows = np.zeros((maxs + 1, 13))
         M = self.L.og_trace_ray_flat(C.byref(med), R or g.ring_radius, ds or g.ds, xs, ys, gam0, maxs, _d(rows))
-        self._keep = f6
+        self._keep = (f6, al)
         if M < 0:
             raise RuntimeError("ray did not reach the ring")
         return rows[:M + 1]
 
     # a2 + a3 (+ a4 when all fans are traced)
-    def tables(self, f6, fans=None) -> Tables:
+    def tables(self, f6, fans=None, al=None) -> Tables:
+        """Tables of the listed fans (all when None); al: smoothed alpha map for a lossy medium."""
         f6 = _f64(f6)
+        alp = None
+        if al is not None:
+            al = _f64(al)
+            alp = _d(al)
         N, X = self.N, self.X
         fl = np.arange(N, dtype=np.int32) if fans is None else _i32(fans)
         nf = len(fl)
@@ -182,8 +216,8 @@ class Oracle:
         K = np.zeros((nf, X), np.int32); cov = np.zeros((nf, X), np.int32)
         exits = np.zeros((nf, N - 1, 4))
         bad = C.c_long(0)
-        unc = self.L.og_tables(C.byref(self.g), _d(f6), _i(fl), nf, _d(T), _d(a), _d(gam), _i(K), _i(cov),
-                               _d(exits), C.byref(bad))
+        unc = self.L.og_tables_abs(C.byref(self.g), _d(f6), alp, _i(fl), nf, _d(T), _d(a), _d(gam), _i(K),
+                                   _i(cov), _d(exits), C.byref(bad))
         t = Tables(fl, T, a, gam, K, cov, exits, int(unc), int(bad.value))
         if fans is None:
             t.dg = self.dgamma(gam, cov)
@@ -209,6 +243,24 @@ class Oracle:
         D = np.zeros((self.N, self.N), np.complex128)
         self.L.og_forward(C.byref(self.g), f, self.X, _d(T), _d(a), _i(K), _d(v), _d(D.view(np.float64)))
         return D
+
+    def forward_c(self, f: float, T, a, K, v):
+        """D[e, r] = sum_x G_r G_e v with complex v (already Upsilon_m dA dm)."""
+        T, a, K = _f64(T), _f64(a), _i32(K)
+        vf = _cplx_to_f64(v)
+        D = np.zeros((self.N, self.N), np.complex128)
+        self.L.og_forward_c(C.byref(self.g), f, self.X, _d(T), _d(a), _i(K), _d(vf), _d(D.view(np.float64)))
+        return D
+
+    def adjoint_plain_c(self, f: float, T, a, K, ups, R, nodes=None):
+        """dA conj(Upsilon_m) sum conj(G_r G_e) R at the listed nodes (ups: Upsilon_m there)."""
+        T, a, K = _f64(T), _f64(a), _i32(K)
+        Rf, uf = _cplx_to_f64(R), _cplx_to_f64(ups)
+        nodes = np.arange(self.X, dtype=np.int32) if nodes is None else _i32(nodes)
+        out = np.zeros(len(nodes), np.complex128)
+        self.L.og_adjoint_plain_c(C.byref(self.g), f, self.X, _d(T), _d(a), _i(K), _d(uf), _d(Rf), _i(nodes),
+                                  len(nodes), _d(out.view(np.float64)))
+        return out
 
     def adjoint_plain(self, f: float, T, a, K, R, nodes=None):
         T, a, K = _f64(T), _f64(a), _i32(K)
@@ -237,7 +289,30 @@ class Oracle:
         bad = self.L.og_update(C.byref(self.g), f, df, self.X, _i(self.idx), _d(grad_re), _d(c), _d(out), _d(st))
         return out, st, bad
 
+    def update_abs(self, f: float, df: float, grad, c, alpha0, y: float):
+        gf, c, a0 = _cplx_to_f64(grad), _f64(c), _f64(alpha0)
+        out = np.zeros_like(c)
+        st = np.zeros(3)
+        bad = self.L.og_update_abs(C.byref(self.g), f, df, self.X, _i(self.idx), _d(gf), _d(c), _d(a0), y, _d(out),
+                                   _d(st))
+        return out, st, bad
+
     # composites
+    def predict_abs(self, f: float, c, alpha0, y: float):
+        c, a0 = _f64(c), _f64(alpha0)
+        out = np.zeros((self.N, self.N), np.complex128)
+        st = np.zeros(3)
+        self.L.og_predict_abs(C.byref(self.g), f, _d(c), _d(a0), y, _d(out.view(np.float64)), _d(st))
+        return out, st
+
+    def update_frequency_abs(self, f: float, df: float, c, alpha0, y: float, data):
+        c, a0 = _f64(c), _f64(alpha0)
+        dataf = _cplx_to_f64(data)
+        out = np.zeros_like(c)
+        st = np.zeros(7)
+        bad = self.L.og_update_frequency_abs(C.byref(self.g), f, df, _d(c), _d(a0), y, _d(dataf), _d(out), _d(st))
+        return out, st, bad
+
     def predict(self, f: float, c):
         c = _f64(c)
         out = np.zeros((self.N, self.N), np.complex128)
@@ -254,6 +329,13 @@ class Oracle:
         return out, st, bad
 
     # helpers shared by tests
+    @staticmethod
+    def upsilon(f: float, c, alpha0, y: float):
+        """Upsilon_m = omega c k~, k~ = omega/c + alpha0 omega^y (tan(pi y/2) + i) (elementwise)."""
+        w = 2 * np.pi * f
+        c, a0 = np.asarray(c, float), np.asarray(alpha0, float)
+        return w * c * (w / c + a0 * w ** y * (np.tan(np.pi * y / 2) + 1j))
+
     def rough_v(self, f: float, c, ns):
         """v[x] = omega^2 dA (m - m_s) on the mask (Born term of the rough part)."""
         w = 2 * np.pi * f

@@ -25,6 +25,15 @@
  *                                                             btk-amp-angle]
  *   a9  update of the squared slowness                      [Sec. 3.4, m <- m + tau dm]
  *
+ * Absorption and dispersion (Sec. 2.2; the "_abs" entry points): the complex wavenumber
+ * k~ = omega/c + alpha (tan(pi y/2) + i), alpha = alpha0 omega^y (Eq. szabo_dispersion_equation).
+ * Rays follow the real part k = omega n_e, n_e = 1/c + alpha0 tan(pi y/2) omega^(y-1)
+ * (Eqs. wave-number, eikonal), so the phase is omega times the travel time on n_e
+ * (Eq. phase-discretised); the amplitude gains A_abs = exp(-int alpha ds) along the ray
+ * (Eqs. absorption, amplitude-abs-discretised); the scattering potential is
+ * Upsilon_m = omega c k~ (Eq. scattering-potential); the preconditioner's
+ * |d|kbar|/d omega| carries the extra term y tan(pi y/2) omega^(y-1) alpha0.
+ *
  * Readings where the paper is silent or ambiguous are listed in the design doc; the
  * ones that change arithmetic are restated beside the code below.
  */
@@ -58,9 +67,10 @@ typedef struct {
     double dx, x0, y0;
     const double *f;        /* [6][ny][nx] */
     double c1, gx, gy;
+    const double *al;       /* absorption coefficient alpha [ny][nx] in Np/m, NULL: lossless */
 } og_medium;
 
-typedef struct { double n, gx, gy, hxx, hxy, hyy; } fval;
+typedef struct { double n, gx, gy, hxx, hxy, hyy, al; } fval;
 
 /* ------------------------------------------------------------------ a1 */
 
@@ -99,6 +109,50 @@ void og_smooth(const og_geom *g, const double *c, int w, double *ns)
         }
     free(n);
     free(t);
+}
+
+/* Separable moving average of width w of an arbitrary map, edges replicated (the same
+ * filter as og_smooth). */
+static void box_smooth(const og_geom *g, const double *in, int w, double *out)
+{
+    int h = w / 2, nx = g->nx, ny = g->ny;
+    double *t = malloc(sizeof(double) * nx * ny);
+    for (int iy = 0; iy < ny; iy++)
+        for (int ix = 0; ix < nx; ix++) {
+            double s = 0;
+            for (int d = -h; d <= h; d++) s += in[iy * nx + clampi(ix + d, 0, nx - 1)];
+            t[iy * nx + ix] = s / w;
+        }
+    for (int iy = 0; iy < ny; iy++)
+        for (int ix = 0; ix < nx; ix++) {
+            double s = 0;
+            for (int d = -h; d <= h; d++) s += t[clampi(iy + d, 0, ny - 1) * nx + ix];
+            out[iy * nx + ix] = s / w;
+        }
+    free(t);
+}
+
+/* Smoothing with absorption (Sec. 6.2: the wavenumber map is smoothed before tracing).
+ * Reading: the complex wavenumber map k~ / omega = n_e + i alpha0 omega^(y-1) is smoothed
+ * by the same window, i.e. both the ray slowness n_e = 1/c + alpha0 tan(pi y/2) omega^(y-1)
+ * (Eq. wave-number) and the absorption coefficient alpha = alpha0 omega^y. Outputs:
+ * ns = smoothed 1/c (the smooth background of the Born split, m_s = ns^2), ne = smoothed
+ * n_e (the field the rays follow), as = smoothed alpha (Np/m). alpha0 in Np (rad/s)^-y m^-1. */
+void og_smooth_abs(const og_geom *g, const double *c, const double *alpha0, double y, double f, int w, double *ns,
+                   double *ne, double *as)
+{
+    size_t P = (size_t)g->nx * g->ny;
+    double om = 2 * M_PI * f, tn = tan(M_PI * y / 2) * pow(om, y - 1), wy = pow(om, y);
+    double *a = malloc(sizeof(double) * P), *b = malloc(sizeof(double) * P), *q = malloc(sizeof(double) * P);
+    for (size_t k = 0; k < P; k++) {
+        a[k] = 1.0 / c[k];
+        b[k] = 1.0 / c[k] + alpha0[k] * tn;
+        q[k] = alpha0[k] * wy;
+    }
+    box_smooth(g, a, w, ns);
+    box_smooth(g, b, w, ne);
+    box_smooth(g, q, w, as);
+    free(a); free(b); free(q);
 }
 
 /* Central differences of the smoothed slowness (edge indices clamped). */
@@ -149,6 +203,7 @@ static void field_eval(const og_medium *m, double px, double py, fval *o)
         o->hxx = 2 * m->gx * m->gx / (c * c * c);
         o->hxy = 2 * m->gx * m->gy / (c * c * c);
         o->hyy = 2 * m->gy * m->gy / (c * c * c);
+        o->al = 0;
         return;
     }
     double u = (px - m->x0) / m->dx, v = (py - m->y0) / m->dx;
@@ -162,6 +217,11 @@ static void field_eval(const og_medium *m, double px, double py, fval *o)
         r[q] = w00 * F[k] + w10 * F[k + 1] + w01 * F[k + m->nx] + w11 * F[k + m->nx + 1];
     }
     o->n = r[0]; o->gx = r[1]; o->gy = r[2]; o->hxx = r[3]; o->hxy = r[4]; o->hyy = r[5];
+    o->al = 0;
+    if (m->al) {
+        const double *F = m->al;
+        o->al = w00 * F[k] + w10 * F[k + 1] + w01 * F[k + m->nx] + w11 * F[k + m->nx + 1];
+    }
 }
 
 /* ------------------------------------------------------------------ a2 */
@@ -171,11 +231,11 @@ static void field_eval(const og_medium *m, double px, double py, fval *o)
  * A_geom = (8 pi omega / c0)^(-1/2) * a, a_i = [ (c_i / c_1) |J_1 / J_i| / ds ]^(1/2),
  * with the reference amplitude [8 pi k0 |x_1 - x_0|]^(-1/2) and |x_1 - x_0| = ds. */
 typedef struct {
-    double x, y, T, J, a, gam, n, dH, px, py;
+    double x, y, T, J, a, gam, n, dH, px, py, B;
     int K;
 } osample;
 
-#define SAMPLE_DOUBLES 12
+#define SAMPLE_DOUBLES 13
 
 /* Trace one ray from (xs,ys) with initial direction gam0 until it crosses radius R.
  * Samples 0..M are written to out (M returned), -1 if maxs steps are exceeded.
@@ -184,7 +244,9 @@ typedef struct {
  * system do not depend on omega, so p = k / omega and dp = dk / omega are carried.
  * Reading of Alg. 1: both stages of the paraxial update use the reference-ray
  * quantities of the same stage (p, grad n, Hess n at x; p', grad n', Hess n' at
- * x + ds q_x). Travel time is the trapezoid rule of n along the samples. */
+ * x + ds q_x). Travel time is the trapezoid rule of n along the samples; with absorption
+ * B = int alpha ds uses the same rule and the sample amplitude is a exp(-B) (A = A_abs A_geom,
+ * Eqs. amplitude-abs-discretised, amplitude-geom-discretised). */
 int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, double gam0, int maxs,
                  osample *out)
 {
@@ -194,7 +256,7 @@ int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, 
     double px = n * cos(gam0), py = n * sin(gam0);
     /* paraxial initial condition: dx = 0, p . dp = 0 (Sec. 4.4, initial conditions) */
     double dxx = 0, dxy = 0, dpx = -n * sin(gam0), dpy = n * cos(gam0);
-    double T = 0;
+    double T = 0, B = 0;
     int K = 0;
     double J1 = 0, n1 = 0, Jlast = 0;
     memset(&out[0], 0, sizeof(osample));
@@ -233,7 +295,7 @@ int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, 
         double dxxn = dxx + ds * (qdxx + qdxax) / 2, dxyn = dxy + ds * (qdxy + qdxay) / 2;
         double dpxn = dpx + ds * (qdpx + qdpax) / 2, dpyn = dpy + ds * (qdpy + qdpay) / 2;
         field_eval(m, xn, yn, &H);
-        double Tn = T + ds * (n + H.n) / 2;
+        double Tn = T + ds * (n + H.n) / 2, Bn = B + ds * (F.al + H.al) / 2;
         int last = 0;
         if (xn * xn + yn * yn >= R * R) {
             /* final partial step ds' <= ds landing on the ring (Def. ray-parameterisation):
@@ -247,13 +309,14 @@ int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, 
             double fr = t / ds;
             xn = x + t * dirx; yn = y + t * diry;
             Tn = T + fr * (Tn - T);
+            Bn = B + fr * (Bn - B);
             dxxn = dxx + fr * (dxxn - dxx); dxyn = dxy + fr * (dxyn - dxy);
             dpxn = dpx + fr * (dpxn - dpx); dpyn = dpy + fr * (dpyn - dpy);
             pxn = px + fr * (pxn - px); pyn = py + fr * (pyn - py);
             field_eval(m, xn, yn, &H);
             last = 1;
         }
-        x = xn; y = yn; px = pxn; py = pyn; dxx = dxxn; dxy = dxyn; dpx = dpxn; dpy = dpyn; T = Tn;
+        x = xn; y = yn; px = pxn; py = pyn; dxx = dxxn; dxy = dxyn; dpx = dpxn; dpy = dpyn; T = Tn; B = Bn;
         /* sample i+1 */
         double pm = sqrt(px * px + py * py), tx = px / pm, ty = py / pm;
         double J = dxx * ty - dxy * tx;
@@ -263,7 +326,8 @@ int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, 
         osample *s = &out[i + 1];
         s->x = x; s->y = y; s->T = T; s->J = J; s->n = H.n; s->px = px; s->py = py; s->K = K;
         s->gam = atan2(py, px);
-        s->a = sqrt((n1 / H.n) * fabs(J1 / J) / ds);
+        s->a = sqrt((n1 / H.n) * fabs(J1 / J) / ds) * exp(-B);
+        s->B = B;
         /* paraxial condition dH = grad_p H . dp + grad_x H . dx, H = (p.p - n^2) / (2n) */
         double pp = px * px + py * py;
         double hx = -H.gx * (pp + H.n * H.n) / (2 * H.n * H.n), hy = -H.gy * (pp + H.n * H.n) / (2 * H.n * H.n);
@@ -274,7 +338,7 @@ int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, 
 }
 
 /* Flat-array wrapper used by the tests: rows of SAMPLE_DOUBLES doubles
- * (x, y, T, J, a, gamma, K, n, dH, px, py, s). */
+ * (x, y, T, J, a, gamma, K, n, dH, px, py, s, B). */
 int og_trace_ray_flat(const og_medium *m, double R, double ds, double xs, double ys, double gam0, int maxs,
                       double *rows)
 {
@@ -284,7 +348,7 @@ int og_trace_ray_flat(const og_medium *m, double R, double ds, double xs, double
     for (int i = 0; i < cnt; i++) {
         double *r = rows + (size_t)i * SAMPLE_DOUBLES;
         r[0] = s[i].x; r[1] = s[i].y; r[2] = s[i].T; r[3] = s[i].J; r[4] = s[i].a; r[5] = s[i].gam;
-        r[6] = s[i].K; r[7] = s[i].n; r[8] = s[i].dH; r[9] = s[i].px; r[10] = s[i].py;
+        r[6] = s[i].K; r[7] = s[i].n; r[8] = s[i].dH; r[9] = s[i].px; r[10] = s[i].py; r[12] = s[i].B;
         r[11] = (i == M && M > 0) ? (M - 1) * ds + sqrt((s[i].x - s[i - 1].x) * (s[i].x - s[i - 1].x) +
                                                         (s[i].y - s[i - 1].y) * (s[i].y - s[i - 1].y))
                                   : i * ds;
@@ -404,15 +468,26 @@ static int fan_tables(const og_geom *g, const og_medium *med, const int *node2x,
  * Row q of each output (X entries) belongs to fan fans[q]. Uncovered mask nodes get
  * T = 0, a = 0, gamma = 0, K = 0 and covered = 0. Returns the number of uncovered
  * (fan, node) entries; *bad_rays counts rays that never reached the ring. */
+long og_tables_abs(const og_geom *g, const double *f6, const double *al, const int *fans, int nf, double *T,
+                   double *a, double *gam, int *K, int *covered, double *exits, long *bad_rays);
+
 long og_tables(const og_geom *g, const double *f6, const int *fans, int nf, double *T, double *a, double *gam,
                int *K, int *covered, double *exits, long *bad_rays)
+{
+    return og_tables_abs(g, f6, NULL, fans, nf, T, a, gam, K, covered, exits, bad_rays);
+}
+
+/* og_tables on a lossy medium: al = smoothed absorption coefficient alpha [ny][nx] (Np/m),
+ * NULL for a lossless one; the tables' a then holds A_geom A_abs / (8 pi omega / c0)^(-1/2). */
+long og_tables_abs(const og_geom *g, const double *f6, const double *al, const int *fans, int nf, double *T,
+                   double *a, double *gam, int *K, int *covered, double *exits, long *bad_rays)
 {
     int X = og_mask(g, NULL);
     int *idx = malloc(sizeof(int) * X), *node2x = malloc(sizeof(int) * g->nx * g->ny);
     og_mask(g, idx);
     for (int k = 0; k < g->nx * g->ny; k++) node2x[k] = -1;
     for (int k = 0; k < X; k++) node2x[idx[k]] = k;
-    og_medium med = {0, g->nx, g->ny, g->dx, g->x0, g->y0, f6, 0, 0, 0};
+    og_medium med = {0, g->nx, g->ny, g->dx, g->x0, g->y0, f6, 0, 0, 0, al};
     long unc = 0, bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : unc, bad)
     for (int q = 0; q < nf; q++) {
@@ -562,6 +637,69 @@ void og_forward(const og_geom *g, double f, int X, const double *T, const double
     free(G);
 }
 
+/* og_forward with a complex v[x] = Upsilon_m dm[x] Delta A (interleaved re, im), the lossy
+ * scattering potential Upsilon_m = omega c k~ (Eq. scattering-potential). */
+void og_forward_c(const og_geom *g, double f, int X, const double *T, const double *a, const int *K, const double *v,
+                  double *D)
+{
+    int N = g->N;
+    double w = 2 * M_PI * f;
+    double *G = malloc(sizeof(double) * 2 * (size_t)N * X);
+#pragma omp parallel for
+    for (int e = 0; e < N; e++)
+        for (int k = 0; k < X; k++) {
+            size_t i = (size_t)e * X + k;
+            double Gd[2];
+            green(w, g->c0, T[i], a[i], K[i], &G[2 * i], Gd);
+        }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int e = 0; e < N; e++)
+        for (int r = 0; r < N; r++) {
+            double sr = 0, si = 0;
+            const double *Ge = G + 2 * (size_t)e * X, *Gr = G + 2 * (size_t)r * X;
+            for (int k = 0; k < X; k++) {
+                double pr = Gr[2 * k] * Ge[2 * k] - Gr[2 * k + 1] * Ge[2 * k + 1];
+                double pi = Gr[2 * k] * Ge[2 * k + 1] + Gr[2 * k + 1] * Ge[2 * k];
+                sr += pr * v[2 * k] - pi * v[2 * k + 1];
+                si += pr * v[2 * k + 1] + pi * v[2 * k];
+            }
+            D[2 * ((size_t)e * N + r)] = sr;
+            D[2 * ((size_t)e * N + r) + 1] = si;
+        }
+    free(G);
+}
+
+/* Plain adjoint of og_forward_c: out[x] = dA conj(Upsilon_m[x]) sum_{e,r} conj(G_r G_e) R,
+ * ups[x] = Upsilon_m at the listed nodes (interleaved). */
+void og_adjoint_plain_c(const og_geom *g, double f, int X, const double *T, const double *a, const int *K,
+                        const double *ups, const double *Rm, const int *nodes, int nn, double *out)
+{
+    int N = g->N;
+    double w = 2 * M_PI * f, dA = g->dx * g->dx;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int q = 0; q < nn; q++) {
+        int k = nodes[q];
+        double *G = malloc(sizeof(double) * 2 * N), Gd[2];
+        for (int e = 0; e < N; e++) {
+            size_t i = (size_t)e * X + k;
+            green(w, g->c0, T[i], a[i], K[i], &G[2 * e], Gd);
+        }
+        double sr = 0, si = 0;
+        for (int e = 0; e < N; e++)
+            for (int r = 0; r < N; r++) {
+                double pr = G[2 * r] * G[2 * e] - G[2 * r + 1] * G[2 * e + 1];
+                double pi = G[2 * r] * G[2 * e + 1] + G[2 * r + 1] * G[2 * e];
+                const double *R = Rm + 2 * ((size_t)e * N + r);
+                sr += pr * R[0] + pi * R[1];
+                si += pr * R[1] - pi * R[0];
+            }
+        double ur = ups[2 * q], ui = -ups[2 * q + 1];
+        out[2 * q] = dA * (ur * sr - ui * si);
+        out[2 * q + 1] = dA * (ur * si + ui * sr);
+        free(G);
+    }
+}
+
 /* Plain adjoint of og_forward: out[x] = omega^2 dA sum_{e,r} conj(G_r[x] G_e[x]) R[e*N + r]
  * (the Q = 1 gradient of Eq. functional-gradient). nodes: mask indices to evaluate. */
 void og_adjoint_plain(const og_geom *g, double f, int X, const double *T, const double *a, const int *K,
@@ -669,6 +807,52 @@ int og_update(const og_geom *g, double f, double df, int X, const int *idx, cons
     return bad;
 }
 
+/* Scattering potential Upsilon_m = omega c k~ at a node (Eq. scattering-potential) with
+ * k~ = omega/c + alpha0 omega^y (tan(pi y/2) + i) (Eq. szabo_dispersion_equation). */
+static void upsilon(double w, double c, double alpha0, double y, double *u)
+{
+    double al = alpha0 * pow(w, y);
+    u[0] = w * c * (w / c + al * tan(M_PI * y / 2));
+    u[1] = w * c * al;
+}
+
+/* og_update with absorption: the node factor m/omega of the lossless update becomes
+ * |kbar| |d|kbar|/d omega| / (4 cos^2(theta/2) Upsilon_m) = k (1/c + y tan(pi y/2) omega^(y-1) alpha0) / Upsilon_m
+ * (Eqs. btk-amp-angle and the derivative of |kbar| in Sec. 3.3, Eq. scattering-potential), complex,
+ * so dm = -(Delta omega / (2 pi)^3) Re{ factor * grad } with grad the complex unfactorised sum of
+ * og_backproject. c and alpha0 are the node's current (unsmoothed) values. */
+int og_update_abs(const og_geom *g, double f, double df, int X, const int *idx, const double *grad,
+                  const double *c_in, const double *alpha0, double y, double *c_out, double *stats)
+{
+    double w = 2 * M_PI * f, dw = 2 * M_PI * df, pref = dw / pow(2 * M_PI, 3);
+    double tn = tan(M_PI * y / 2);
+    int bad = 0;
+    double s2 = 0, mx = 0, dm2 = 0;
+    for (int k = 0; k < g->nx * g->ny; k++) c_out[k] = g->c0;
+    for (int q = 0; q < X; q++) {
+        int k = idx[q];
+        double c = c_in[k], m = 1.0 / (c * c), a0 = alpha0[k];
+        double kr = w / c + a0 * tn * pow(w, y);
+        double num = kr * (1.0 / c + y * tn * pow(w, y - 1) * a0);
+        double u[2];
+        upsilon(w, c, a0, y, u);
+        double un = u[0] * u[0] + u[1] * u[1];
+        double fr = num * u[0] / un, fi = -num * u[1] / un;           /* num / Upsilon_m */
+        double dm = -pref * (fr * grad[2 * q] - fi * grad[2 * q + 1]);
+        double mn = m + g->tau * dm;
+        if (!(mn > 0)) { bad = 1; mn = m; }
+        c_out[k] = 1.0 / sqrt(mn);
+        double dc = c_out[k] - c_in[k];
+        s2 += dc * dc;
+        if (fabs(dc) > mx) mx = fabs(dc);
+        dm2 += dm * dm;
+    }
+    stats[0] = sqrt(s2 / X);
+    stats[1] = mx;
+    stats[2] = sqrt(dm2);
+    return bad;
+}
+
 /* ------------------------------------------------------------------ composites */
 
 typedef struct {
@@ -679,7 +863,8 @@ typedef struct {
     long uncovered, bad_rays;
 } og_state;
 
-static void state_build(const og_geom *g, double f, const double *c, og_state *s)
+static void state_build_abs(const og_geom *g, double f, const double *c, const double *alpha0, double y,
+                            og_state *s)
 {
     size_t P = (size_t)g->nx * g->ny;
     s->X = og_mask(g, NULL);
@@ -687,15 +872,31 @@ static void state_build(const og_geom *g, double f, const double *c, og_state *s
     og_mask(g, s->idx);
     s->ns = malloc(sizeof(double) * P);
     s->f6 = malloc(sizeof(double) * 6 * P);
-    og_smooth(g, c, og_window(g, f), s->ns);
-    og_fields(g, s->ns, s->f6);
+    double *ne = NULL, *as = NULL;
+    if (alpha0) {
+        ne = malloc(sizeof(double) * P);
+        as = malloc(sizeof(double) * P);
+        og_smooth_abs(g, c, alpha0, y, f, og_window(g, f), s->ns, ne, as);
+        og_fields(g, ne, s->f6);
+        free(ne);
+    } else {
+        og_smooth(g, c, og_window(g, f), s->ns);
+        og_fields(g, s->ns, s->f6);
+    }
     size_t NX = (size_t)g->N * s->X;
     s->T = malloc(sizeof(double) * NX); s->a = malloc(sizeof(double) * NX);
     s->gam = malloc(sizeof(double) * NX); s->dg = malloc(sizeof(double) * NX);
     s->K = malloc(sizeof(int) * NX); s->cov = malloc(sizeof(int) * NX);
     s->exits = malloc(sizeof(double) * (size_t)g->N * (g->N - 1) * 4);
-    s->uncovered = og_tables(g, s->f6, NULL, g->N, s->T, s->a, s->gam, s->K, s->cov, s->exits, &s->bad_rays);
+    s->uncovered = og_tables_abs(g, s->f6, as, NULL, g->N, s->T, s->a, s->gam, s->K, s->cov, s->exits,
+                                 &s->bad_rays);
     og_dgamma(g, s->X, s->gam, s->cov, s->dg);
+    free(as);
+}
+
+static void state_build(const og_geom *g, double f, const double *c, og_state *s)
+{
+    state_build_abs(g, f, c, NULL, 0.0, s);
 }
 
 static void state_free(og_state *s)
@@ -767,6 +968,74 @@ int og_update_frequency(const og_geom *g, double f, double df, const double *c, 
     stats[0] = st[0]; stats[1] = st[1]; stats[2] = st[2]; stats[3] = r2;
     stats[4] = s.uncovered; stats[5] = s.bad_rays; stats[6] = cl;
     free(v); free(D); free(R); free(nodes); free(gr); free(gre);
+    state_free(&s);
+    return bad;
+}
+
+/* og_predict on a lossy medium (alpha0 [ny][nx], exponent y): rays on the smoothed n_e with
+ * the absorbing amplitude, and the Born term with v = Upsilon_m dA (m - m_s), m_s = (smoothed
+ * 1/c)^2 (the absorption map is known, not perturbed). */
+void og_predict_abs(const og_geom *g, double f, const double *c, const double *alpha0, double y, double *out,
+                    double *stats)
+{
+    og_state s;
+    state_build_abs(g, f, c, alpha0, y, &s);
+    int N = g->N;
+    double w = 2 * M_PI * f, dA = g->dx * g->dx;
+    double *v = malloc(sizeof(double) * 2 * s.X), *D = malloc(sizeof(double) * 2 * (size_t)N * N);
+    for (int q = 0; q < s.X; q++) {
+        int k = s.idx[q];
+        double u[2], dm = 1.0 / (c[k] * c[k]) - s.ns[k] * s.ns[k];
+        upsilon(w, c[k], alpha0[k], y, u);
+        v[2 * q] = u[0] * dA * dm;
+        v[2 * q + 1] = u[1] * dA * dm;
+    }
+    long cl = og_direct_green(g, f, s.exits, out);
+    og_forward_c(g, f, s.X, s.T, s.a, s.K, v, D);
+    for (size_t i = 0; i < 2 * (size_t)N * N; i++) out[i] += D[i];
+    for (int e = 0; e < N; e++) out[2 * ((size_t)e * N + e)] = out[2 * ((size_t)e * N + e) + 1] = 0;
+    if (stats) { stats[0] = s.uncovered; stats[1] = s.bad_rays; stats[2] = cl; }
+    free(v); free(D);
+    state_free(&s);
+}
+
+/* og_update_frequency on a lossy medium (see og_predict_abs, og_update_abs). */
+int og_update_frequency_abs(const og_geom *g, double f, double df, const double *c, const double *alpha0, double y,
+                            const double *data, double *c_out, double *stats)
+{
+    og_state s;
+    state_build_abs(g, f, c, alpha0, y, &s);
+    int N = g->N;
+    double w = 2 * M_PI * f, dA = g->dx * g->dx;
+    double *v = malloc(sizeof(double) * 2 * s.X), *D = malloc(sizeof(double) * 2 * (size_t)N * N);
+    double *R = malloc(sizeof(double) * 2 * (size_t)N * N);
+    for (int q = 0; q < s.X; q++) {
+        int k = s.idx[q];
+        double u[2], dm = 1.0 / (c[k] * c[k]) - s.ns[k] * s.ns[k];
+        upsilon(w, c[k], alpha0[k], y, u);
+        v[2 * q] = u[0] * dA * dm;
+        v[2 * q + 1] = u[1] * dA * dm;
+    }
+    long cl = og_direct_green(g, f, s.exits, R);
+    og_forward_c(g, f, s.X, s.T, s.a, s.K, v, D);
+    double r2 = 0;
+    for (int e = 0; e < N; e++)
+        for (int r = 0; r < N; r++) {
+            size_t i = 2 * ((size_t)e * N + r);
+            if (r == e) { R[i] = R[i + 1] = 0; continue; }
+            R[i] += D[i] - data[i];
+            R[i + 1] += D[i + 1] - data[i + 1];
+            r2 += R[i] * R[i] + R[i + 1] * R[i + 1];
+        }
+    int *nodes = malloc(sizeof(int) * s.X);
+    for (int q = 0; q < s.X; q++) nodes[q] = q;
+    double *gr = malloc(sizeof(double) * 2 * s.X);
+    og_backproject(g, f, s.X, s.T, s.a, s.gam, s.K, s.dg, R, nodes, s.X, gr);
+    double st[3];
+    int bad = og_update_abs(g, f, df, s.X, s.idx, gr, c, alpha0, y, c_out, st);
+    stats[0] = st[0]; stats[1] = st[1]; stats[2] = st[2]; stats[3] = r2;
+    stats[4] = s.uncovered; stats[5] = s.bad_rays; stats[6] = cl;
+    free(v); free(D); free(R); free(nodes); free(gr);
     state_free(&s);
     return bad;
 }
