@@ -108,6 +108,17 @@ rbx_status rbx_mask(rbx_job *job, int *X_out, int *idx_dev);
  * any value is not finite and positive (checked on the device, synchronises). */
 rbx_status rbx_set_model(rbx_job *job, const float *c_dev);
 
+/* Absorption and dispersion (Sec. 2.2, Szabo's power law): alpha0_dev is the absorption map
+ * alpha0 [ny*nx] (float32, device, copied; Np (rad/s)^-y m^-1, alpha = alpha0 omega^y >= 0)
+ * of the medium, known during the sound-speed inversion; y the power-law exponent (0 < y < 2,
+ * y != 1). Rays then follow 1/c + alpha0 tan(pi y/2) omega^(y-1) (smoothed with the same
+ * window as the lossless slowness), table amplitudes include exp(-int alpha ds), the Born
+ * weights use Upsilon_m = omega c k~ and the update the lossy node factor (see
+ * rbx_update_frequency). alpha0_dev == NULL returns the job to a lossless medium. Call after
+ * rbx_set_geometry (which clears it); rays must be traced again afterwards.
+ * Errors: RBX_EINVAL (bad y, negative or non-finite alpha0), RBX_ESTATE, RBX_ENOMEM. */
+rbx_status rbx_set_absorption(rbx_job *job, const float *alpha0_dev, double y);
+
 /* Copy the job's current sound-speed map out (ny*nx float32, device). */
 rbx_status rbx_get_model(rbx_job *job, float *c_dev);
 

@@ -94,30 +94,67 @@ __global__ void k_smooth_y(const double *__restrict__ t, double *__restrict__ ns
     ns[iy * nx + ix] = (float)s;
 }
 
-// Central differences of the smoothed slowness (edge indices clamped).
-__global__ void k_fields(const double *__restrict__ ns, float *__restrict__ F, int nx, int ny, double dx)
+// Moving average of width w along x of an arbitrary map (edges replicated).
+__global__ void k_smooth_x_map(const float *__restrict__ a, double *__restrict__ t, int nx, int ny, int w)
 {
     int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
     if (ix >= nx) return;
-    auto at = [&](int i, int j) { return ns[clampi(j, 0, ny - 1) * nx + clampi(i, 0, nx - 1)]; };
+    int h = (w - 1) / 2;
+    double s = 0;
+    for (int d = -h; d <= h; d++) s += (double)a[iy * nx + clampi(ix + d, 0, nx - 1)];
+    t[iy * nx + ix] = s / w;
+}
+
+__global__ void k_smooth_y_map(const double *__restrict__ t, double *__restrict__ out, int nx, int ny, int w)
+{
+    int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+    if (ix >= nx) return;
+    int h = (w - 1) / 2;
+    double s = 0;
+    for (int d = -h; d <= h; d++) s += t[clampi(iy + d, 0, ny - 1) * nx + ix];
+    out[iy * nx + ix] = s / w;
+}
+
+// Central differences of the smoothed ray slowness (edge indices clamped). Lossless: the
+// smoothed 1/c. Lossy (as != nullptr): n_e = smoothed 1/c + tn * smoothed alpha0 with
+// tn = tan(pi y/2) omega^(y-1) (the box filter is linear, so this is the smoothed real
+// wavenumber map over omega), and the record's slot 6 holds alpha = wy * smoothed alpha0.
+__global__ void k_fields(const double *__restrict__ ns, const double *__restrict__ as, double tn, double wy,
+                         float *__restrict__ F, int nx, int ny, double dx)
+{
+    int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
+    if (ix >= nx) return;
+    auto at = [&](int i, int j) {
+        const size_t k = (size_t)clampi(j, 0, ny - 1) * nx + clampi(i, 0, nx - 1);
+        return as ? ns[k] + tn * as[k] : ns[k];
+    };
     double c = at(ix, iy);
     double fx = (at(ix + 1, iy) - at(ix - 1, iy)) / (2 * dx);
     double fy = (at(ix, iy + 1) - at(ix, iy - 1)) / (2 * dx);
     double fxx = (at(ix + 1, iy) - 2 * c + at(ix - 1, iy)) / (dx * dx);
     double fxy = (at(ix + 1, iy + 1) - at(ix - 1, iy + 1) - at(ix + 1, iy - 1) + at(ix - 1, iy - 1)) / (4 * dx * dx);
     double fyy = (at(ix, iy + 1) - 2 * c + at(ix, iy - 1)) / (dx * dx);
+    const float al = as ? (float)(wy * as[(size_t)iy * nx + ix]) : 0.f;
     float4 *o = reinterpret_cast<float4 *>(F + (size_t)(iy * nx + ix) * kFieldStride);
     o[0] = make_float4((float)c, (float)fx, (float)fy, (float)fxx);
-    o[1] = make_float4((float)fxy, (float)fyy, 0.f, 0.f);
+    o[1] = make_float4((float)fxy, (float)fyy, al, 0.f);
 }
 
 void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *tmp64, double *ns64, float *ns,
-                          float *fields, cudaStream_t s)
+                          float *fields, const Lossy &ab, double f, cudaStream_t s)
 {
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
     k_smooth_x<<<grd, blk, 0, s>>>(c, tmp64, g.nx, g.ny, w);
     k_smooth_y<<<grd, blk, 0, s>>>(tmp64, ns64, ns, g.nx, g.ny, w);
-    k_fields<<<grd, blk, 0, s>>>(ns64, fields, g.nx, g.ny, g.dx);
+    double tn = 0.0, wy = 0.0;
+    if (ab.alpha0) {
+        const double PI = 3.14159265358979323846, om = 2.0 * PI * f;
+        tn = tan(PI * ab.y / 2.0) * pow(om, ab.y - 1.0);
+        wy = pow(om, ab.y);
+        k_smooth_x_map<<<grd, blk, 0, s>>>(ab.alpha0, tmp64, g.nx, g.ny, w);
+        k_smooth_y_map<<<grd, blk, 0, s>>>(tmp64, ab.as64, g.nx, g.ny, w);
+    }
+    k_fields<<<grd, blk, 0, s>>>(ns64, ab.alpha0 ? ab.as64 : nullptr, tn, wy, fields, g.nx, g.ny, g.dx);
 }
 
 __global__ void k_check_model(const float *c, int n, unsigned long long *flag)
@@ -132,6 +169,17 @@ __global__ void k_check_model(const float *c, int n, unsigned long long *flag)
 void launch_check_model(const float *c, int n, unsigned long long *flag, cudaStream_t s)
 {
     k_check_model<<<(n + 255) / 256, 256, 0, s>>>(c, n, flag);
+}
+
+__global__ void k_check_alpha(const float *a, int n, unsigned long long *flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(a[i] >= 0.f && isfinite(a[i]))) atomicAdd(flag, 1ull);
+}
+
+void launch_check_alpha(const float *a, int n, unsigned long long *flag, cudaStream_t s)
+{
+    k_check_alpha<<<(n + 255) / 256, 256, 0, s>>>(a, n, flag);
 }
 
 __global__ void k_fill(float *p, float v, size_t n)

@@ -95,37 +95,63 @@ void launch_synth_bp(const TabEntry *tab, const float *dg, int N, int X, double 
     k_synth_bp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, dg, n, fhi, flo, green_const(f, c0), U, kap);
 }
 
-// v[x] = omega^2 dA (m - m_s) on the mask: Born weight of the rough part of the model
-// (Eq. scattering-potential with Upsilon_m = omega^2 for a lossless medium).
+// Scattering potential Upsilon_m = omega c k~ (Eq. scattering-potential), with
+// k~ = omega/c + alpha0 omega^y (tan(pi y/2) + i) (Eq. szabo_dispersion_equation):
+// (omega^2 + omega c alpha tan(pi y/2), omega c alpha), alpha = alpha0 omega^y; omega^2 lossless.
+__device__ __forceinline__ double2 upsilon_m(double w, double c, double alpha, double tn)
+{
+    return make_double2(w * w + w * c * alpha * tn, w * c * alpha);
+}
+
+// v[x] = Upsilon_m dA (m - m_s) on the mask: Born weight of the rough part of the model.
 __global__ void k_born_rough(const float *__restrict__ c, const double *__restrict__ ns, const int *__restrict__ idx,
-                             int X, double scale, float *__restrict__ v)
+                             int X, double w, double dA, const float *__restrict__ alpha0, double wy, double tn,
+                             float2 *__restrict__ v)
 {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= X) return;
     int k = idx[q];
     double cc = c[k], n = ns[k];
-    v[q] = (float)(scale * (1.0 / (cc * cc) - n * n));
+    double2 u = upsilon_m(w, cc, alpha0 ? wy * (double)alpha0[k] : 0.0, tn);
+    double d = dA * (1.0 / (cc * cc) - n * n);
+    v[q] = make_float2((float)(u.x * d), (float)(u.y * d));
 }
 
-__global__ void k_born_dm(const float *__restrict__ dm, const int *__restrict__ idx, int X, double scale,
-                          float *__restrict__ v)
+__global__ void k_born_dm(const float *__restrict__ dm, const float *__restrict__ c, const int *__restrict__ idx, int X,
+                          double w, double dA, const float *__restrict__ alpha0, double wy, double tn,
+                          float2 *__restrict__ v)
 {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= X) return;
-    v[q] = (float)(scale * (double)dm[idx[q]]);
+    int k = idx[q];
+    double2 u = alpha0 ? upsilon_m(w, (double)c[k], wy * (double)alpha0[k], tn) : make_double2(w * w, 0.0);
+    double d = dA * (double)dm[k];
+    v[q] = make_float2((float)(u.x * d), (float)(u.y * d));
+}
+
+static void lossy_factors(const Lossy &ab, double w, double &wy, double &tn)
+{
+    wy = tn = 0.0;
+    if (ab.alpha0) {
+        wy = pow(w, ab.y);
+        tn = tan(3.14159265358979323846 * ab.y / 2.0);
+    }
 }
 
 void launch_born_weights_rough(const float *c, const double *ns64, const int *idx, int X, double f, double dA,
-                               float *v, cudaStream_t s)
+                               const Lossy &ab, float2 *v, cudaStream_t s)
 {
-    double w = 2.0 * 3.14159265358979323846 * f;
-    k_born_rough<<<(X + 255) / 256, 256, 0, s>>>(c, ns64, idx, X, w * w * dA, v);
+    double w = 2.0 * 3.14159265358979323846 * f, wy, tn;
+    lossy_factors(ab, w, wy, tn);
+    k_born_rough<<<(X + 255) / 256, 256, 0, s>>>(c, ns64, idx, X, w, dA, ab.alpha0, wy, tn, v);
 }
 
-void launch_born_weights_dm(const float *dm, const int *idx, int X, double f, double dA, float *v, cudaStream_t s)
+void launch_born_weights_dm(const float *dm, const float *c, const int *idx, int X, double f, double dA,
+                            const Lossy &ab, float2 *v, cudaStream_t s)
 {
-    double w = 2.0 * 3.14159265358979323846 * f;
-    k_born_dm<<<(X + 255) / 256, 256, 0, s>>>(dm, idx, X, w * w * dA, v);
+    double w = 2.0 * 3.14159265358979323846 * f, wy, tn;
+    lossy_factors(ab, w, wy, tn);
+    k_born_dm<<<(X + 255) / 256, 256, 0, s>>>(dm, c, idx, X, w, dA, ab.alpha0, wy, tn, v);
 }
 
 // ---------------------------------------------------------------- forward
@@ -142,7 +168,7 @@ int forward_splits(int N, int X)
     return s < 1 ? 1 : s;
 }
 
-__global__ __launch_bounds__(256) void k_forward_simt(const float2 *__restrict__ G, const float *__restrict__ v, int N,
+__global__ __launch_bounds__(256) void k_forward_simt(const float2 *__restrict__ G, const float2 *__restrict__ v, int N,
                                                       int X, int xchunk, float2 *__restrict__ part)
 {
     // upper-triangular tile pair from the linear block index
@@ -163,14 +189,14 @@ __global__ __launch_bounds__(256) void k_forward_simt(const float2 *__restrict__
     for (int x0 = xb; x0 < xe; x0 += TK) {
         int x = x0 + lk;
         bool ok = x < xe;
-        float vv = ok ? v[x] : 0.f;
+        const float2 vv = ok ? v[x] : make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             int row = lr + 16 * q;
             int e = te * TM + row, r = tr * TM + row;
             As[lk][row] = (ok && e < N) ? G[(size_t)e * X + x] : make_float2(0.f, 0.f);
             float2 g = (ok && r < N) ? G[(size_t)r * X + x] : make_float2(0.f, 0.f);
-            Bs[lk][row] = make_float2(g.x * vv, g.y * vv);
+            Bs[lk][row] = make_float2(g.x * vv.x - g.y * vv.y, g.x * vv.y + g.y * vv.x);
         }
         __syncthreads();
 #pragma unroll
@@ -197,7 +223,7 @@ __global__ __launch_bounds__(256) void k_forward_simt(const float2 *__restrict__
         }
 }
 
-void launch_forward_simt(const float2 *G, const float *v, int N, int X, int splits, float2 *part, cudaStream_t s)
+void launch_forward_simt(const float2 *G, const float2 *v, int N, int X, int splits, float2 *part, cudaStream_t s)
 {
     int T = (N + TM - 1) / TM, pairs = T * (T + 1) / 2;
     int xchunk = (X + splits - 1) / splits;

@@ -373,7 +373,7 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
 
 // planes [4][Npad][Xpad]: Gre, Gim, (G v)re, (G v)im (then 4 lo planes when split);
 // G_e[x] = C a exp(i 2 pi (f T - K/4 + 1/8))
-__global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float *__restrict__ v, int N, int X, int Xpad,
+__global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *__restrict__ v, int N, int X, int Xpad,
                                size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes,
                                int split)
 {
@@ -388,13 +388,13 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float *__
         gr = C * t.a * c;
         gi = C * t.a * s;
     }
-    float vv = v[x];
+    const float2 vv = v[x];
     size_t o = (size_t)e * Xpad + x;
     __nv_bfloat16 *lo = split ? planes + 4 * pstride : nullptr;
     put_split(planes + o, lo ? lo + o : nullptr, gr);
     put_split(planes + pstride + o, lo ? lo + pstride + o : nullptr, gi);
-    put_split(planes + 2 * pstride + o, lo ? lo + 2 * pstride + o : nullptr, gr * vv);
-    put_split(planes + 3 * pstride + o, lo ? lo + 3 * pstride + o : nullptr, gi * vv);
+    put_split(planes + 2 * pstride + o, lo ? lo + 2 * pstride + o : nullptr, gr * vv.x - gi * vv.y);
+    put_split(planes + 3 * pstride + o, lo ? lo + 3 * pstride + o : nullptr, gr * vv.y + gi * vv.x);
 }
 
 // planes [6][Xp][Npad] at [x][e]: u, conj(kappa) u, kappa u (re, im each);
@@ -667,7 +667,7 @@ static float green_const_tc(double f, double c0)
     return (float)(1.0 / sqrt(8.0 * 3.14159265358979323846 * (2.0 * 3.14159265358979323846 * f) / c0));
 }
 
-void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, cudaStream_t s)
+void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s)
 {
     size_t n = (size_t)p.N * p.X;
     float fhi = (float)f, flo = (float)(f - (double)fhi);

@@ -123,12 +123,39 @@ void launch_combine_adjoint(const float2 *gpart, int X, int mode, int weight_mod
     k_combine<<<(X + 255) / 256, 256, 0, s>>>(gpart, X, mode, weight_mode == 0 ? -1.f : 1.f, scale, out);
 }
 
+// plain adjoint on a lossy medium: out[x] = dA conj(Upsilon_m) g0[x], Upsilon_m = omega c k~
+__global__ void k_combine_lossy(const float2 *__restrict__ gpart, const float *__restrict__ c,
+                                const float *__restrict__ alpha0, const int *__restrict__ idx, int X, double w,
+                                double wy, double tn, double dA, float2 *__restrict__ out)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= X) return;
+    const int k = idx[x];
+    const double cc = c[k], al = wy * (double)alpha0[k];
+    const double ur = w * w + w * cc * al * tn, ui = -w * cc * al;       // conj(Upsilon_m)
+    const double gr = gpart[x].x, gi = gpart[x].y;
+    out[x] = make_float2((float)(dA * (ur * gr - ui * gi)), (float)(dA * (ur * gi + ui * gr)));
+}
+
+void launch_combine_adjoint_lossy(const float2 *gpart, const float *c, const int *idx, int X, double f, double dA,
+                                  const Lossy &ab, float2 *out, cudaStream_t s)
+{
+    const double PI = 3.14159265358979323846, w = 2 * PI * f;
+    k_combine_lossy<<<(X + 255) / 256, 256, 0, s>>>(gpart, c, ab.alpha0, idx, X, w, pow(w, ab.y),
+                                                    tan(PI * ab.y / 2), dA, out);
+}
+
 // red layout (nb = update blocks): [0,nb) sum dc^2, [nb,2nb) max |dc|, [2nb,3nb) sum dm^2,
 // totals at [3nb], [3nb+1], [3nb+2]
+// Lossless: dm = -(Delta omega/(2 pi)^3) (m/omega) Re grad. Lossy (alpha0 != nullptr): the node
+// factor m/omega becomes k (1/c + y tan(pi y/2) omega^(y-1) alpha0) / Upsilon_m with
+// k = omega/c + alpha0 tan(pi y/2) omega^y (the derivative of |kbar| in Sec. 3.3 and
+// Eq. scattering-potential), complex, and dm = -(Delta omega/(2 pi)^3) Re{factor grad}.
 __global__ __launch_bounds__(RB) void k_update(const float2 *__restrict__ gpart, const int *__restrict__ node2x, int X,
                                                int nxy, float sgn, double pref_over_w, double tau, float c0,
                                                float *__restrict__ c, double *__restrict__ red,
-                                               unsigned long long *counters)
+                                               unsigned long long *counters, const float *__restrict__ alpha0,
+                                               double w, double y, double wy, double tn)
 {
     __shared__ double sh[RB];
     int k = blockIdx.x * RB + threadIdx.x;
@@ -141,7 +168,18 @@ __global__ __launch_bounds__(RB) void k_update(const float2 *__restrict__ gpart,
             double grad = 2.0 * ((double)gpart[xi].x + sgn * (double)gpart[(size_t)X + xi].x);
             double cold = c[k];
             double m = 1.0 / (cold * cold);
-            double dm = -pref_over_w * m * grad;
+            double dm;
+            if (alpha0) {
+                const double a0 = alpha0[k], al = a0 * wy;
+                const double gim = 2.0 * ((double)gpart[xi].y + sgn * (double)gpart[(size_t)X + xi].y);
+                const double kr = w / cold + al * tn;
+                const double num = kr * (1.0 / cold + y * tn * (wy / w) * a0);
+                const double ur = w * w + w * cold * al * tn, ui = w * cold * al, un = ur * ur + ui * ui;
+                const double fr = num * ur / un, fi = -num * ui / un;
+                dm = -pref_over_w * w * (fr * grad - fi * gim);
+            } else {
+                dm = -pref_over_w * m * grad;
+            }
             double mn = m + tau * dm;
             if (!(mn > 0.0) || !isfinite(mn)) {
                 atomicAdd(&counters[4], 1ull);
@@ -180,14 +218,15 @@ __global__ void k_final_update(const double *__restrict__ red, int nb, double *_
 
 void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X, int weight_mode, double f,
                    double df, double tau, double c0, float *c, double *red, unsigned long long *counters,
-                   cudaStream_t s)
+                   const Lossy &ab, cudaStream_t s)
 {
     const double PI = 3.14159265358979323846;
     double w = 2 * PI * f, dw = 2 * PI * df;
     double pref = dw / (8 * PI * PI * PI);
     int nb = update_blocks(nx, ny);
+    const double wy = ab.alpha0 ? pow(w, ab.y) : 0.0, tn = ab.alpha0 ? tan(PI * ab.y / 2) : 0.0;
     k_update<<<nb, RB, 0, s>>>(gpart, node2x, X, nx * ny, weight_mode == 0 ? -1.f : 1.f, pref / w, tau, (float)c0, c,
-                               red, counters);
+                               red, counters, ab.alpha0, w, ab.y, wy, tn);
     k_final_update<<<1, 32, 0, s>>>(red, nb, red + 3 * nb);
 }
 

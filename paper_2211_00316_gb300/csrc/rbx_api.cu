@@ -21,10 +21,12 @@ enum { EV_START, EV_FIELDS, EV_TRACE, EV_TABLES, EV_GDIR, EV_SYNTH_F, EV_GEMM_F,
 
 struct rbx_job {
     cudaStream_t stream = nullptr;
-    bool own_stream = false;
     rbx_geometry g{};
     bool has_geom = false, has_tables = false, ns_valid = false;
     int ns_window = 0;
+    double ns_freq = 0.0;      // frequency the fields were made for (lossy fields depend on it)
+    bool lossy = false;        // absorption map set (rbx_set_absorption)
+    double abs_y = 0.0;
     Workspace w;
     int *d_count = nullptr;
     std::string err;
@@ -84,7 +86,7 @@ static cudaError_t dalloc(T *&p, size_t n, cudaStream_t s)
 static void free_ws(Workspace &w, cudaStream_t s)
 {
     void *ps[] = {w.hist, w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
-                  w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters};
+                  w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters, w.alpha0, w.as64};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, s);
     tc_free(w.tc, s);
@@ -145,7 +147,6 @@ rbx_status rbx_destroy(rbx_job *j)
     cudaStreamSynchronize(j->stream);
     for (int k = 0; k < EV_COUNT; k++)
         if (j->ev[k]) cudaEventDestroy(j->ev[k]);
-    if (j->own_stream) cudaStreamDestroy(j->stream);
     delete j;
     return RBX_OK;
 }
@@ -183,7 +184,7 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     free_ws(j->w, j->stream);
     keep_pool_memory();
-    j->has_geom = j->has_tables = j->ns_valid = false;
+    j->has_geom = j->has_tables = j->ns_valid = j->lossy = false;
     Workspace &w = j->w;
     w.N = g.n_xducers;
     w.nx = g.nx;
@@ -287,6 +288,38 @@ rbx_status rbx_set_model(rbx_job *j, const float *c_dev)
     return RBX_OK;
 }
 
+rbx_status rbx_set_absorption(rbx_job *j, const float *alpha0_dev, double y)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_set_absorption before rbx_set_geometry");
+    j->ns_valid = j->has_tables = false;
+    if (!alpha0_dev) {
+        j->lossy = false;
+        return RBX_OK;
+    }
+    NEED(j, std::isfinite(y) && y > 0.0 && y < 2.0 && std::fabs(y - 1.0) > 1e-6, RBX_EINVAL,
+         "power-law exponent y must lie in (0, 2) and differ from 1 (tan(pi y/2) is finite)");
+    Workspace &w = j->w;
+    const size_t nxy = (size_t)w.nx * w.ny;
+    if (!w.alpha0) {
+        if (dalloc(w.alpha0, nxy, j->stream) != cudaSuccess || dalloc(w.as64, nxy, j->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(j, RBX_ENOMEM, "device allocation of the absorption map failed");
+        }
+    }
+    CUDA_TRY(j, cudaMemcpyAsync(w.alpha0, alpha0_dev, nxy * sizeof(float), cudaMemcpyDeviceToDevice, j->stream));
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 5, 0, sizeof(unsigned long long), j->stream));
+    launch_check_alpha(w.alpha0, (int)nxy, w.counters + 5, j->stream);
+    LAUNCHED(j, 1);
+    unsigned long long bad = 0;
+    CUDA_TRY(j, cudaMemcpyAsync(&bad, w.counters + 5, sizeof bad, cudaMemcpyDeviceToHost, j->stream));
+    CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+    NEED(j, bad == 0, RBX_EINVAL, "absorption coefficients must be finite and >= 0");
+    j->lossy = true;
+    j->abs_y = y;
+    return RBX_OK;
+}
+
 rbx_status rbx_get_model(rbx_job *j, float *c_dev)
 {
     if (!j || !c_dev) return RBX_EINVAL;
@@ -296,14 +329,26 @@ rbx_status rbx_get_model(rbx_job *j, float *c_dev)
     return RBX_OK;
 }
 
+static Lossy lossy_of(const rbx_job *j)
+{
+    Lossy ab;
+    if (j->lossy) {
+        ab.alpha0 = j->w.alpha0;
+        ab.as64 = j->w.as64;
+        ab.y = j->abs_y;
+    }
+    return ab;
+}
+
 static rbx_status smooth(rbx_job *j, double f)
 {
     int w = window_for(f, j->g.dx);
-    if (j->ns_valid && j->ns_window == w) return RBX_OK;
-    launch_smooth_fields(j->g, j->w.c, w, j->w.tmp64, j->w.ns64, j->w.ns, j->w.fields, j->stream);
-    LAUNCHED(j, 3);
+    if (j->ns_valid && j->ns_window == w && (!j->lossy || j->ns_freq == f)) return RBX_OK;
+    launch_smooth_fields(j->g, j->w.c, w, j->w.tmp64, j->w.ns64, j->w.ns, j->w.fields, lossy_of(j), f, j->stream);
+    LAUNCHED(j, j->lossy ? 5 : 3);
     j->ns_valid = true;
     j->ns_window = w;
+    j->ns_freq = f;
     return RBX_OK;
 }
 
@@ -330,7 +375,7 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     p.maxs = max_steps(j->g);
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
     launch_uniform_radius(w.fields, p, w.counters + 7, j->stream);
-    launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->stream);
+    launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->lossy, j->stream);
     LAUNCHED(j, 2);
     if ((st = record(j, EV_TRACE))) return st;
     launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
@@ -414,7 +459,7 @@ rbx_status rbx_forward(rbx_job *j, double f, const float *dm_dev, void *D_dev)
     NEED(j, j->has_tables, RBX_ESTATE, "rbx_forward before rbx_trace_rays or rbx_set_tables");
     NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
     Workspace &w = j->w;
-    launch_born_weights_dm(dm_dev, w.idx, w.X, f, j->g.dx * j->g.dx, w.v, j->stream);
+    launch_born_weights_dm(dm_dev, w.c, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
     LAUNCHED(j, 1);
     rbx_status st = forward_core(j, f, false);
     if (st) return st;
@@ -431,7 +476,7 @@ rbx_status rbx_predict(rbx_job *j, double f, void *g_dev)
     rbx_status st;
     if ((st = smooth(j, f))) return st;
     launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
-    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, w.v, j->stream);
+    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
     LAUNCHED(j, 2);
     if ((st = forward_core(j, f, false))) return st;
     launch_add_offdiag(w.gdir, w.D, w.N, static_cast<float2 *>(g_dev), j->stream);
@@ -460,8 +505,12 @@ rbx_status rbx_adjoint(rbx_job *j, double f, const void *R_dev, void *out_dev, i
         double om = 2 * 3.14159265358979323846 * f;
         launch_synth_fwd(w.tab, w.N, w.X, f, j->g.c0, w.G, j->stream);
         launch_backproject_simt(w.G, nullptr, w.Rs, w.N, w.X, 1, w.gpart, j->stream);
-        launch_combine_adjoint(w.gpart, w.X, 1, j->g.weight_mode, om * om * j->g.dx * j->g.dx,
-                               static_cast<float2 *>(out_dev), j->stream);
+        if (j->lossy)
+            launch_combine_adjoint_lossy(w.gpart, w.c, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j),
+                                         static_cast<float2 *>(out_dev), j->stream);
+        else
+            launch_combine_adjoint(w.gpart, w.X, 1, j->g.weight_mode, om * om * j->g.dx * j->g.dx,
+                                   static_cast<float2 *>(out_dev), j->stream);
     }
     LAUNCHED(j, 3);
     return RBX_OK;
@@ -478,7 +527,7 @@ static rbx_status enqueue_update(rbx_job *j, double f, double df, const float2 *
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 1, 0, sizeof(unsigned long long), j->stream));
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 4, 0, sizeof(unsigned long long), j->stream));
     launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
-    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, w.v, j->stream);
+    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
     LAUNCHED(j, 2);
     if ((st = record(j, EV_GDIR))) return st;
     if ((st = forward_core(j, f, true))) return st;
@@ -501,7 +550,7 @@ static rbx_status enqueue_update(rbx_job *j, double f, double df, const float2 *
     if ((st = record(j, EV_GEMM_B))) return st;
     const int roff = residual_blocks(w.N) + 8;
     launch_update(w.gpart, w.node2x, w.nx, w.ny, w.X, j->g.weight_mode, f, df, j->g.tau, j->g.c0, w.c, w.red + roff,
-                  w.counters, j->stream);
+                  w.counters, lossy_of(j), j->stream);
     launch_snapshot(w.red + residual_blocks(w.N), w.red + roff + 3 * update_blocks(w.nx, w.ny), w.counters,
                     w.tc.err, w.hist + (size_t)slot * kHistStride, j->stream);
     LAUNCHED(j, 3);

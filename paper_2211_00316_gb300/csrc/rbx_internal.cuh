@@ -8,7 +8,7 @@
 
 namespace rbx {
 
-constexpr int kFieldStride = 8;          // floats per node: n, n_x, n_y, n_xx, n_xy, n_yy, 0, 0
+constexpr int kFieldStride = 8;          // floats per node: n, n_x, n_y, n_xx, n_xy, n_yy, alpha, 0
 constexpr uint32_t kUncovered = 0xFFFFFFFFu;
 constexpr int kMaxSteps = 2047;          // ray samples index i < 2048 (11 bits of the key)
 constexpr int kMaxXducers = 4095;        // ray index j < 4096 (12 bits of the key)
@@ -60,7 +60,9 @@ struct Workspace {
     float *dg = nullptr;
     float4 *exits = nullptr;
     float2 *G = nullptr, *U = nullptr, *kap = nullptr;
-    float *v = nullptr;
+    float2 *v = nullptr;        // Born weight Upsilon_m dA (m - m_s) per mask node (complex when lossy)
+    float *alpha0 = nullptr;    // absorption map alpha0 [ny][nx], Np (rad/s)^-y m^-1 (lossy jobs only)
+    double *as64 = nullptr;     // smoothed alpha0 (lossy jobs only)
     float2 *gdir = nullptr, *D = nullptr, *R = nullptr, *Rs = nullptr, *part = nullptr, *gpart = nullptr;
     float2 *data = nullptr;
     double *red = nullptr;           // reduction scratch
@@ -74,15 +76,23 @@ struct Workspace {
 // k_fields.cu
 void launch_mask(const rbx_geometry &g, int *node2x, int *count, cudaStream_t s);
 void launch_mask_idx(const int *node2x, int nxy, int *idx, cudaStream_t s);
+// Absorption of a lossy job (Szabo power law): alpha = alpha0 omega^y, rays on
+// 1/c + alpha0 tan(pi y/2) omega^(y-1). alpha0 == nullptr: lossless.
+struct Lossy {
+    const float *alpha0 = nullptr;
+    double *as64 = nullptr;
+    double y = 0.0;
+};
 void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *tmp64, double *ns64, float *ns,
-                          float *fields, cudaStream_t s);
+                          float *fields, const Lossy &ab, double f, cudaStream_t s);
 void launch_check_model(const float *c, int n, unsigned long long *flag, cudaStream_t s);
+void launch_check_alpha(const float *a, int n, unsigned long long *flag, cudaStream_t s);
 void launch_fill(float *p, float v, size_t n, cudaStream_t s);
 
 // k_rays.cu
 void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s);
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
-                         unsigned long long *counters, cudaStream_t s);
+                         unsigned long long *counters, bool lossy, cudaStream_t s);
 void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s);
 void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, unsigned long long *counters, cudaStream_t s);
 void launch_direct_green(const float4 *exits, int N, double f, double c0, float2 *g, unsigned long long *counters,
@@ -95,11 +105,14 @@ void launch_get_tables(const TabEntry *tab, float *T, float *a, float *gam, uint
 void launch_synth_fwd(const TabEntry *tab, int N, int X, double f, double c0, float2 *G, cudaStream_t s);
 void launch_synth_bp(const TabEntry *tab, const float *dg, int N, int X, double f, double c0, float2 *U,
                      float2 *kap, cudaStream_t s);
+// Born weights v[x] = Upsilon_m dA (m - m_s) (rough part) or Upsilon_m dA dm[x], with
+// Upsilon_m = omega c k~ at the node (omega^2 when lossless; c = current model).
 void launch_born_weights_rough(const float *c, const double *ns64, const int *idx, int X, double f, double dA,
-                               float *v, cudaStream_t s);
-void launch_born_weights_dm(const float *dm, const int *idx, int X, double f, double dA, float *v, cudaStream_t s);
+                               const Lossy &ab, float2 *v, cudaStream_t s);
+void launch_born_weights_dm(const float *dm, const float *c, const int *idx, int X, double f, double dA,
+                            const Lossy &ab, float2 *v, cudaStream_t s);
 int forward_splits(int N, int X);
-void launch_forward_simt(const float2 *G, const float *v, int N, int X, int splits, float2 *part, cudaStream_t s);
+void launch_forward_simt(const float2 *G, const float2 *v, int N, int X, int splits, float2 *part, cudaStream_t s);
 void launch_forward_reduce(const float2 *part, int N, int splits, float2 *D, cudaStream_t s);
 // mode 0: preconditioned (A = U, conj(kap) U; W = U, kap U); mode 1: plain adjoint (A = W = conj(G))
 void launch_backproject_simt(const float2 *A, const float2 *kap, const float2 *Rs, int N, int X, int mode,
@@ -112,7 +125,7 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t s);
 bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s);
 int set_autotune(int mode);
 void tc_free(TcPlanes &p, cudaStream_t s);
-void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float *v, double f, double c0, cudaStream_t s);
+void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s);
 int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s);
 void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, double f, double c0, cudaStream_t s);
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s);
@@ -123,9 +136,12 @@ void launch_residual(const float2 *gdir, const float2 *D, const float2 *data, in
 void launch_symmetrize(const float2 *R, int N, float2 *Rs, cudaStream_t s);
 void launch_combine_adjoint(const float2 *gpart, int X, int mode, int weight_mode, double scale, float2 *out,
                             cudaStream_t s);
+// plain adjoint of a lossy job: out[x] = dA conj(Upsilon_m[x]) gpart[x]
+void launch_combine_adjoint_lossy(const float2 *gpart, const float *c, const int *idx, int X, double f, double dA,
+                                  const Lossy &ab, float2 *out, cudaStream_t s);
 void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X, int weight_mode, double f,
                    double df, double tau, double c0, float *c, double *red, unsigned long long *counters,
-                   cudaStream_t s);
+                   const Lossy &ab, cudaStream_t s);
 void launch_snapshot(const double *r2, const double *upd3, const unsigned long long *counters, const unsigned *tc_err,
                      double *slot, cudaStream_t s);
 int residual_blocks(int N);

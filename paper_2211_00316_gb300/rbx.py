@@ -81,6 +81,7 @@ _SIGS = {
     "rbx_server_poll": [_P, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double), _P, C.POINTER(Stats)],
     "rbx_server_wait": [_P, C.c_longlong, C.c_double],
     "rbx_server_cancel": [_P, C.c_longlong],
+    "rbx_set_absorption": [_P, _P, C.c_double],
     "rbx_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
     "rbx_server_times": [_P, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -202,6 +203,15 @@ class Job:
 
     def set_model(self, c: torch.Tensor):
         self._check(self.L.rbx_set_model(self.h, _ptr(c)))
+
+    def set_absorption(self, alpha0: torch.Tensor | None, y: float = 1.4):
+        """Absorption map alpha0 [ny][nx] (Np (rad/s)^-y m^-1, float32 on the device) and
+        power-law exponent y; None returns to a lossless medium (rbx_set_absorption)."""
+        if alpha0 is None:
+            self._check(self.L.rbx_set_absorption(self.h, None, float(y)))
+            return
+        a = alpha0.contiguous().to(torch.float32)
+        self._check(self.L.rbx_set_absorption(self.h, _ptr(a), float(y)))
 
     def get_model(self) -> torch.Tensor:
         out = torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda")
