@@ -443,6 +443,8 @@ def main():
     ap.add_argument("--max-inflight", type=int, default=16)
     ap.add_argument("--closed", type=int, default=64, help="served form: closed-loop burst size (0 = none)")
     ap.add_argument("--no-serial", action="store_true", help="served form: skip the serial plain FP32 replay")
+    ap.add_argument("--absorption", action="store_true",
+                    help="lossy medium: breast absorption map 0-1 dB/(MHz^1.4 cm), y = 1.4 (rbx_set_absorption)")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="default workload: requests of the short served run reported beside throughput (0 = none)")
     args = ap.parse_args()
@@ -478,6 +480,8 @@ def main():
         job = rbx.Job(stream)
         job.set_geometry(g, precision=prec)
         N, X = job.N, job.X
+        if args.absorption:
+            job.set_absorption(torch.tensor(P.absorption_map(w.c_true), dtype=torch.float32, device="cuda"), 1.4)
         # synthetic data: the library's own ray-Born prediction on the true model + 40 dB noise
         job.set_model(torch.tensor(w.c_true, dtype=torch.float32, device="cuda"))
         fidx = [k % len(w.freqs) for k in range(total_steps)]
@@ -581,6 +585,7 @@ def main():
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
             "data": "synthetic (library ray-Born prediction on a seeded breast-like phantom + 40 dB noise)",
             "config": {"workload": describe(w), "mask_nodes": X, "precision": args.precision,
+                       "absorption": ("breast map 0-1 dB/(MHz^1.4 cm), y=1.4" if args.absorption else "none"),
                        "l2": "inputs larger than L2 (tables N*X*16 B = %.2f GB)" % (16.0 * N * X / 1e9),
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": int(sum(s["n_launches"] for s in stats)),

@@ -167,6 +167,17 @@ def breast_phantom(geom: Geometry, seed: int) -> np.ndarray:
     return c
 
 
+def absorption_map(c_true: np.ndarray, c0: float = C_WATER, y: float = 1.4) -> np.ndarray:
+    """Absorption coefficient alpha0 (Np (rad/s)^-y m^-1) of a breast-like phantom, in the
+    paper's range 0-1 dB MHz^-y cm^-1 with water lossless (Sec. 6.1): fat (below c0) 0.4,
+    denser tissue 0.5 + 0.5 (c - 1520)/50 clipped to [0.5, 1.0] dB MHz^-y cm^-1."""
+    c = np.asarray(c_true, float)
+    db = np.where(c < c0 - 1e-9, 0.4, np.clip(0.5 + 0.5 * (c - 1520.0) / 50.0, 0.5, 1.0))
+    db = np.where(np.abs(c - c0) <= 1e-9, 0.0, db)
+    np_per_m = db * 100.0 / (20.0 * np.log10(np.e))
+    return np_per_m / (2 * np.pi * 1e6) ** y
+
+
 def add_noise(data: np.ndarray, snr_db: float, seed: int) -> np.ndarray:
     """Complex Gaussian noise, E|n|^2 = sigma^2, sigma = 10^(-SNR/20) * max off-diagonal |data|.
 
