@@ -53,7 +53,7 @@ class OGeom(C.Structure):
 class OMedium(C.Structure):
     _fields_ = [("mode", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("x0", C.c_double),
                 ("y0", C.c_double), ("f", C.POINTER(C.c_double)), ("c1", C.c_double), ("gx", C.c_double),
-                ("gy", C.c_double), ("al", C.POINTER(C.c_double))]
+                ("gy", C.c_double), ("al", C.POINTER(C.c_double)), ("nr", C.POINTER(C.c_double))]
 
 
 _D = C.POINTER(C.c_double)
@@ -96,6 +96,12 @@ def _declare(L):
     L.og_predict_abs.argtypes = [_G, C.c_double, _D, _D, C.c_double, _D, _D]; L.og_predict_abs.restype = None
     L.og_update_frequency_abs.argtypes = [_G, C.c_double, C.c_double, _D, _D, C.c_double, _D, _D, _D]
     L.og_update_frequency_abs.restype = C.c_int
+    L.og_tables_ext.argtypes = [_G, _D, _D, _D, _I, C.c_int, _D, _D, _D, _I, _I, _D, C.POINTER(C.c_long)]
+    L.og_tables_ext.restype = C.c_long
+    L.og_predict_ext.argtypes = [_G, C.c_double, _D, _D, C.c_double, C.c_int, _D, _D]
+    L.og_predict_ext.restype = None
+    L.og_update_set_ext.argtypes = [_G, _D, C.c_int, C.c_double, _D, _D, C.c_double, C.c_int, _D, _D, _D]
+    L.og_update_set_ext.restype = C.c_int
 
 
 def _d(a):
@@ -180,35 +186,44 @@ class Oracle:
         return ns, self.fields(ne), al
 
     # a2
-    def trace_ray(self, xs, ys, gam0, f6=None, linear=None, maxs=None, R=None, ds=None, al=None):
-        """Samples of one ray: columns x, y, T, J, a, gamma, K, n, dH, px, py, s, B (al: alpha map)."""
+    def trace_ray(self, xs, ys, gam0, f6=None, linear=None, maxs=None, R=None, ds=None, al=None, nr=None):
+        """Samples of one ray: columns x, y, T, J, a, gamma, K, n, dH, px, py, s, B (al: alpha map,
+        nr: slowness integrated along the ray)."""
         g = self.geom
         maxs = maxs or int(np.ceil(3 * g.ring_radius / (ds or g.ds))) + 8
         if linear is not None:
             c1, gx, gy = linear
-            med = OMedium(1, g.nx, g.ny, g.dx, g.x0, g.y0, None, c1, gx, gy, None)
+            med = OMedium(1, g.nx, g.ny, g.dx, g.x0, g.y0, None, c1, gx, gy, None, None)
         else:
             f6 = _f64(f6)
             alp = None
             if al is not None:
                 al = _f64(al)
                 alp = _d(al)
-            med = OMedium(0, g.nx, g.ny, g.dx, g.x0, g.y0, _d(f6), 0.0, 0.0, 0.0, alp)
+            nrp = None
+            if nr is not None:
+                nr = _f64(nr)
+                nrp = _d(nr)
+            med = OMedium(0, g.nx, g.ny, g.dx, g.x0, g.y0, _d(f6), 0.0, 0.0, 0.0, alp, nrp)
         rows = np.zeros((maxs + 1, 13))
         M = self.L.og_trace_ray_flat(C.byref(med), R or g.ring_radius, ds or g.ds, xs, ys, gam0, maxs, _d(rows))
-        self._keep = (f6, al)
+        self._keep = (f6, al, nr)
         if M < 0:
             raise RuntimeError("ray did not reach the ring")
         return rows[:M + 1]
 
     # a2 + a3 (+ a4 when all fans are traced)
-    def tables(self, f6, fans=None, al=None) -> Tables:
-        """Tables of the listed fans (all when None); al: smoothed alpha map for a lossy medium."""
+    def tables(self, f6, fans=None, al=None, nr=None) -> Tables:
+        """Tables of the listed fans (all when None); al: alpha map of a lossy medium; nr: the
+        slowness integrated along the rays (default: the traced, smoothed one)."""
         f6 = _f64(f6)
-        alp = None
+        alp = nrp = None
         if al is not None:
             al = _f64(al)
             alp = _d(al)
+        if nr is not None:
+            nr = _f64(nr)
+            nrp = _d(nr)
         N, X = self.N, self.X
         fl = np.arange(N, dtype=np.int32) if fans is None else _i32(fans)
         nf = len(fl)
@@ -216,7 +231,7 @@ class Oracle:
         K = np.zeros((nf, X), np.int32); cov = np.zeros((nf, X), np.int32)
         exits = np.zeros((nf, N - 1, 4))
         bad = C.c_long(0)
-        unc = self.L.og_tables_abs(C.byref(self.g), _d(f6), alp, _i(fl), nf, _d(T), _d(a), _d(gam), _i(K),
+        unc = self.L.og_tables_ext(C.byref(self.g), _d(f6), alp, nrp, _i(fl), nf, _d(T), _d(a), _d(gam), _i(K),
                                    _i(cov), _d(exits), C.byref(bad))
         t = Tables(fl, T, a, gam, K, cov, exits, int(unc), int(bad.value))
         if fans is None:
@@ -311,6 +326,28 @@ class Oracle:
         out = np.zeros_like(c)
         st = np.zeros(7)
         bad = self.L.og_update_frequency_abs(C.byref(self.g), f, df, _d(c), _d(a0), y, _d(dataf), _d(out), _d(st))
+        return out, st, bad
+
+    def predict_ext(self, f: float, c, alpha0=None, y: float = 1.4, raw: bool = False):
+        """Predicted data; raw: integration on the non-smoothed map, no Born term (Sec. 6.3.2)."""
+        c = _f64(c)
+        a0 = None if alpha0 is None else _f64(alpha0)
+        out = np.zeros((self.N, self.N), np.complex128)
+        st = np.zeros(3)
+        self.L.og_predict_ext(C.byref(self.g), f, _d(c), None if a0 is None else _d(a0), y, int(raw),
+                              _d(out.view(np.float64)), _d(st))
+        return out, st
+
+    def update_set(self, freqs, df: float, c, data, alpha0=None, y: float = 1.4, raw: bool = False):
+        """One update from a frequency set (data: [nf][N][N])."""
+        fr = np.ascontiguousarray(freqs, dtype=np.float64)
+        c = _f64(c)
+        a0 = None if alpha0 is None else _f64(alpha0)
+        dataf = _cplx_to_f64(data)
+        out = np.zeros_like(c)
+        st = np.zeros(7)
+        bad = self.L.og_update_set_ext(C.byref(self.g), _d(fr), len(fr), df, _d(c), None if a0 is None else _d(a0),
+                                       y, int(raw), _d(dataf), _d(out), _d(st))
         return out, st, bad
 
     def predict(self, f: float, c):

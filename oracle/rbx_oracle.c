@@ -68,9 +68,10 @@ typedef struct {
     const double *f;        /* [6][ny][nx] */
     double c1, gx, gy;
     const double *al;       /* absorption coefficient alpha [ny][nx] in Np/m, NULL: lossless */
+    const double *nr;       /* slowness integrated along the rays [ny][nx]; NULL: the traced n */
 } og_medium;
 
-typedef struct { double n, gx, gy, hxx, hxy, hyy, al; } fval;
+typedef struct { double n, gx, gy, hxx, hxy, hyy, al, nr; } fval;
 
 /* ------------------------------------------------------------------ a1 */
 
@@ -204,6 +205,7 @@ static void field_eval(const og_medium *m, double px, double py, fval *o)
         o->hxy = 2 * m->gx * m->gy / (c * c * c);
         o->hyy = 2 * m->gy * m->gy / (c * c * c);
         o->al = 0;
+        o->nr = o->n;
         return;
     }
     double u = (px - m->x0) / m->dx, v = (py - m->y0) / m->dx;
@@ -221,6 +223,11 @@ static void field_eval(const og_medium *m, double px, double py, fval *o)
     if (m->al) {
         const double *F = m->al;
         o->al = w00 * F[k] + w10 * F[k + 1] + w01 * F[k + m->nx] + w11 * F[k + m->nx + 1];
+    }
+    o->nr = o->n;
+    if (m->nr) {
+        const double *F = m->nr;
+        o->nr = w00 * F[k] + w10 * F[k + 1] + w01 * F[k + m->nx] + w11 * F[k + m->nx + 1];
     }
 }
 
@@ -244,7 +251,9 @@ typedef struct {
  * system do not depend on omega, so p = k / omega and dp = dk / omega are carried.
  * Reading of Alg. 1: both stages of the paraxial update use the reference-ray
  * quantities of the same stage (p, grad n, Hess n at x; p', grad n', Hess n' at
- * x + ds q_x). Travel time is the trapezoid rule of n along the samples; with absorption
+ * x + ds q_x). Travel time is the trapezoid rule of n along the samples (of the unsmoothed
+ * slowness when the medium carries one, Sec. 6.3.2: rays traced on the smoothed map,
+ * integration on the non-smoothed one; the amplitude's c ratio likewise); with absorption
  * B = int alpha ds uses the same rule and the sample amplitude is a exp(-B) (A = A_abs A_geom,
  * Eqs. amplitude-abs-discretised, amplitude-geom-discretised). */
 int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, double gam0, int maxs,
@@ -295,7 +304,7 @@ int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, 
         double dxxn = dxx + ds * (qdxx + qdxax) / 2, dxyn = dxy + ds * (qdxy + qdxay) / 2;
         double dpxn = dpx + ds * (qdpx + qdpax) / 2, dpyn = dpy + ds * (qdpy + qdpay) / 2;
         field_eval(m, xn, yn, &H);
-        double Tn = T + ds * (n + H.n) / 2, Bn = B + ds * (F.al + H.al) / 2;
+        double Tn = T + ds * (F.nr + H.nr) / 2, Bn = B + ds * (F.al + H.al) / 2;
         int last = 0;
         if (xn * xn + yn * yn >= R * R) {
             /* final partial step ds' <= ds landing on the ring (Def. ray-parameterisation):
@@ -320,13 +329,13 @@ int og_trace_ray(const og_medium *m, double R, double ds, double xs, double ys, 
         /* sample i+1 */
         double pm = sqrt(px * px + py * py), tx = px / pm, ty = py / pm;
         double J = dxx * ty - dxy * tx;
-        if (i == 0) { J1 = J; n1 = H.n; Jlast = J; }
+        if (i == 0) { J1 = J; n1 = H.nr; Jlast = J; }
         else if (J * Jlast < 0) { K++; }   /* caustic: sign change of the ray Jacobian */
         if (J != 0) Jlast = J;
         osample *s = &out[i + 1];
         s->x = x; s->y = y; s->T = T; s->J = J; s->n = H.n; s->px = px; s->py = py; s->K = K;
         s->gam = atan2(py, px);
-        s->a = sqrt((n1 / H.n) * fabs(J1 / J) / ds) * exp(-B);
+        s->a = sqrt((n1 / H.nr) * fabs(J1 / J) / ds) * exp(-B);
         s->B = B;
         /* paraxial condition dH = grad_p H . dp + grad_x H . dx, H = (p.p - n^2) / (2n) */
         double pp = px * px + py * py;
@@ -468,8 +477,14 @@ static int fan_tables(const og_geom *g, const og_medium *med, const int *node2x,
  * Row q of each output (X entries) belongs to fan fans[q]. Uncovered mask nodes get
  * T = 0, a = 0, gamma = 0, K = 0 and covered = 0. Returns the number of uncovered
  * (fan, node) entries; *bad_rays counts rays that never reached the ring. */
+long og_tables_ext(const og_geom *g, const double *f6, const double *al, const double *nr, const int *fans, int nf,
+                   double *T, double *a, double *gam, int *K, int *covered, double *exits, long *bad_rays);
+
 long og_tables_abs(const og_geom *g, const double *f6, const double *al, const int *fans, int nf, double *T,
-                   double *a, double *gam, int *K, int *covered, double *exits, long *bad_rays);
+                   double *a, double *gam, int *K, int *covered, double *exits, long *bad_rays)
+{
+    return og_tables_ext(g, f6, al, NULL, fans, nf, T, a, gam, K, covered, exits, bad_rays);
+}
 
 long og_tables(const og_geom *g, const double *f6, const int *fans, int nf, double *T, double *a, double *gam,
                int *K, int *covered, double *exits, long *bad_rays)
@@ -477,17 +492,18 @@ long og_tables(const og_geom *g, const double *f6, const int *fans, int nf, doub
     return og_tables_abs(g, f6, NULL, fans, nf, T, a, gam, K, covered, exits, bad_rays);
 }
 
-/* og_tables on a lossy medium: al = smoothed absorption coefficient alpha [ny][nx] (Np/m),
- * NULL for a lossless one; the tables' a then holds A_geom A_abs / (8 pi omega / c0)^(-1/2). */
-long og_tables_abs(const og_geom *g, const double *f6, const double *al, const int *fans, int nf, double *T,
-                   double *a, double *gam, int *K, int *covered, double *exits, long *bad_rays)
+/* og_tables on a lossy medium: al = absorption coefficient alpha [ny][nx] (Np/m), NULL for a
+ * lossless one (the tables' a then holds A_geom A_abs / (8 pi omega / c0)^(-1/2)); nr = slowness
+ * integrated along the rays (NULL: the traced, smoothed one). */
+long og_tables_ext(const og_geom *g, const double *f6, const double *al, const double *nr, const int *fans, int nf,
+                   double *T, double *a, double *gam, int *K, int *covered, double *exits, long *bad_rays)
 {
     int X = og_mask(g, NULL);
     int *idx = malloc(sizeof(int) * X), *node2x = malloc(sizeof(int) * g->nx * g->ny);
     og_mask(g, idx);
     for (int k = 0; k < g->nx * g->ny; k++) node2x[k] = -1;
     for (int k = 0; k < X; k++) node2x[idx[k]] = k;
-    og_medium med = {0, g->nx, g->ny, g->dx, g->x0, g->y0, f6, 0, 0, 0, al};
+    og_medium med = {0, g->nx, g->ny, g->dx, g->x0, g->y0, f6, 0, 0, 0, al, nr};
     long unc = 0, bad = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : unc, bad)
     for (int q = 0; q < nf; q++) {
@@ -899,6 +915,47 @@ static void state_build(const og_geom *g, double f, const double *c, og_state *s
     state_build_abs(g, f, c, NULL, 0.0, s);
 }
 
+/* State for the paper's integration (Sec. 6.3.2): rays traced on the smoothed map (as in
+ * state_build_abs), travel time, amplitude c ratio and absorption integrated on the
+ * non-smoothed maps 1/c and alpha0 omega^y. */
+static void state_build_raw(const og_geom *g, double f, const double *c, const double *alpha0, double y, og_state *s)
+{
+    size_t P = (size_t)g->nx * g->ny;
+    s->X = og_mask(g, NULL);
+    s->idx = malloc(sizeof(int) * s->X);
+    og_mask(g, s->idx);
+    s->ns = malloc(sizeof(double) * P);
+    s->f6 = malloc(sizeof(double) * 6 * P);
+    double *nr = malloc(sizeof(double) * P), *ar = NULL;
+    for (size_t k = 0; k < P; k++) nr[k] = 1.0 / c[k];
+    if (alpha0) {
+        double *ne = malloc(sizeof(double) * P), *as = malloc(sizeof(double) * P);
+        og_smooth_abs(g, c, alpha0, y, f, og_window(g, f), s->ns, ne, as);
+        og_fields(g, ne, s->f6);
+        free(ne);
+        free(as);
+        ar = malloc(sizeof(double) * P);
+        double wy = pow(2 * M_PI * f, y), tn = tan(M_PI * y / 2) * pow(2 * M_PI * f, y - 1);
+        for (size_t k = 0; k < P; k++) {
+            ar[k] = alpha0[k] * wy;
+            nr[k] += alpha0[k] * tn;        /* the real wavenumber over omega, not smoothed */
+        }
+    } else {
+        og_smooth(g, c, og_window(g, f), s->ns);
+        og_fields(g, s->ns, s->f6);
+    }
+    size_t NX = (size_t)g->N * s->X;
+    s->T = malloc(sizeof(double) * NX); s->a = malloc(sizeof(double) * NX);
+    s->gam = malloc(sizeof(double) * NX); s->dg = malloc(sizeof(double) * NX);
+    s->K = malloc(sizeof(int) * NX); s->cov = malloc(sizeof(int) * NX);
+    s->exits = malloc(sizeof(double) * (size_t)g->N * (g->N - 1) * 4);
+    s->uncovered = og_tables_ext(g, s->f6, ar, nr, NULL, g->N, s->T, s->a, s->gam, s->K, s->cov, s->exits,
+                                 &s->bad_rays);
+    og_dgamma(g, s->X, s->gam, s->cov, s->dg);
+    free(nr);
+    free(ar);
+}
+
 static void state_free(og_state *s)
 {
     free(s->idx); free(s->ns); free(s->f6); free(s->T); free(s->a); free(s->gam); free(s->dg);
@@ -1036,6 +1093,108 @@ int og_update_frequency_abs(const og_geom *g, double f, double df, const double 
     stats[0] = st[0]; stats[1] = st[1]; stats[2] = st[2]; stats[3] = r2;
     stats[4] = s.uncovered; stats[5] = s.bad_rays; stats[6] = cl;
     free(v); free(D); free(R); free(nodes); free(gr);
+    state_free(&s);
+    return bad;
+}
+
+/* Predicted data with the integration mode of the set update below: raw = 0 is og_predict /
+ * og_predict_abs (g_dir + Born term of the rough part); raw = 1 follows Sec. 6.3.2: g at the
+ * ray ends with the phase and amplitude integrated on the non-smoothed map and no Born term
+ * (the rough part is already in the phase). alpha0 may be NULL (lossless). */
+void og_predict_ext(const og_geom *g, double f, const double *c, const double *alpha0, double y, int raw,
+                    double *out, double *stats)
+{
+    if (!raw) {
+        if (alpha0) og_predict_abs(g, f, c, alpha0, y, out, stats);
+        else og_predict(g, f, c, out, stats);
+        return;
+    }
+    og_state s;
+    state_build_raw(g, f, c, alpha0, y, &s);
+    long cl = og_direct_green(g, f, s.exits, out);
+    for (int e = 0; e < g->N; e++) out[2 * ((size_t)e * g->N + e)] = out[2 * ((size_t)e * g->N + e) + 1] = 0;
+    if (stats) { stats[0] = s.uncovered; stats[1] = s.bad_rays; stats[2] = cl; }
+    state_free(&s);
+}
+
+/* One update from a frequency set (Sec. 6.3.2: two consecutive frequencies per update).
+ * Reading: the rays of the set are traced once, on the map smoothed (and, when lossy,
+ * dispersed) for the set's first frequency; each frequency f_k of the set contributes its own
+ * residual R_k and back-projection, and the search direction is the sum over the set of
+ * -(Delta omega/(2 pi)^3) Re{node factor(f_k) grad_k} (Eq. sound_speed_update summed over the
+ * set's omega), applied once with the step tau. raw selects the integration of og_predict_ext.
+ * data: nf complex [N][N] blocks. stats as og_update_frequency, [3] summed over the set. */
+int og_update_set_ext(const og_geom *g, const double *freqs, int nf, double df, const double *c,
+                      const double *alpha0, double y, int raw, const double *data, double *c_out, double *stats)
+{
+    og_state s;
+    if (raw) state_build_raw(g, freqs[0], c, alpha0, y, &s);
+    else state_build_abs(g, freqs[0], c, alpha0, y, &s);
+    int N = g->N;
+    size_t NN = (size_t)N * N;
+    double dA = g->dx * g->dx, pref = 2 * M_PI * df / pow(2 * M_PI, 3), tn = tan(M_PI * y / 2);
+    double *v = malloc(sizeof(double) * 2 * s.X), *D = malloc(sizeof(double) * 2 * NN);
+    double *R = malloc(sizeof(double) * 2 * NN), *gr = malloc(sizeof(double) * 2 * s.X);
+    double *dm = calloc(s.X, sizeof(double));
+    int *nodes = malloc(sizeof(int) * s.X);
+    for (int q = 0; q < s.X; q++) nodes[q] = q;
+    double r2 = 0;
+    long cl = 0;
+    for (int kf = 0; kf < nf; kf++) {
+        double f = freqs[kf], w = 2 * M_PI * f;
+        cl = og_direct_green(g, f, s.exits, R);
+        if (!raw) {
+            for (int q = 0; q < s.X; q++) {
+                int k = s.idx[q];
+                double u[2], d = 1.0 / (c[k] * c[k]) - s.ns[k] * s.ns[k];
+                upsilon(w, c[k], alpha0 ? alpha0[k] : 0.0, alpha0 ? y : 1.0, u);
+                v[2 * q] = u[0] * dA * d;
+                v[2 * q + 1] = u[1] * dA * d;
+            }
+            og_forward_c(g, f, s.X, s.T, s.a, s.K, v, D);
+        } else {
+            memset(D, 0, sizeof(double) * 2 * NN);
+        }
+        const double *dk = data + 2 * NN * kf;
+        for (int e = 0; e < N; e++)
+            for (int r = 0; r < N; r++) {
+                size_t i = 2 * ((size_t)e * N + r);
+                if (r == e) { R[i] = R[i + 1] = 0; continue; }
+                R[i] += D[i] - dk[i];
+                R[i + 1] += D[i + 1] - dk[i + 1];
+                r2 += R[i] * R[i] + R[i + 1] * R[i + 1];
+            }
+        og_backproject(g, f, s.X, s.T, s.a, s.gam, s.K, s.dg, R, nodes, s.X, gr);
+        for (int q = 0; q < s.X; q++) {
+            int k = s.idx[q];
+            double cc = c[k], m = 1.0 / (cc * cc);
+            if (!alpha0) {
+                dm[q] += -pref * (m / w) * gr[2 * q];
+            } else {
+                double a0 = alpha0[k], kr = w / cc + a0 * tn * pow(w, y);
+                double num = kr * (1.0 / cc + y * tn * pow(w, y - 1) * a0), u[2];
+                upsilon(w, cc, a0, y, u);
+                double un = u[0] * u[0] + u[1] * u[1];
+                dm[q] += -pref * (num * u[0] / un * gr[2 * q] + num * u[1] / un * gr[2 * q + 1]);
+            }
+        }
+    }
+    int bad = 0;
+    double s2 = 0, mx = 0, dm2 = 0;
+    for (int k = 0; k < g->nx * g->ny; k++) c_out[k] = g->c0;
+    for (int q = 0; q < s.X; q++) {
+        int k = s.idx[q];
+        double m = 1.0 / (c[k] * c[k]), mn = m + g->tau * dm[q];
+        if (!(mn > 0)) { bad = 1; mn = m; }
+        c_out[k] = 1.0 / sqrt(mn);
+        double dc = c_out[k] - c[k];
+        s2 += dc * dc;
+        if (fabs(dc) > mx) mx = fabs(dc);
+        dm2 += dm[q] * dm[q];
+    }
+    stats[0] = sqrt(s2 / s.X); stats[1] = mx; stats[2] = sqrt(dm2); stats[3] = r2;
+    stats[4] = s.uncovered; stats[5] = s.bad_rays; stats[6] = cl;
+    free(v); free(D); free(R); free(gr); free(dm); free(nodes);
     state_free(&s);
     return bad;
 }
