@@ -119,6 +119,26 @@ rbx_status rbx_set_model(rbx_job *job, const float *c_dev);
  * Errors: RBX_EINVAL (bad y, negative or non-finite alpha0), RBX_ESTATE, RBX_ENOMEM. */
 rbx_status rbx_set_absorption(rbx_job *job, const float *alpha0_dev, double y);
 
+/* Integration mode (Sec. 6.3.2). mode 0 (default): travel times and amplitudes are integrated
+ * on the smoothed map the rays follow, and the predicted data add the Born term of the rough
+ * part m - m_s. mode 1, the paper's implementation: rays are still traced on the smoothed map,
+ * but travel time, the amplitude's slowness ratio and absorption are integrated along them on
+ * the non-smoothed maps, and the predicted data are the ray Green's functions alone (the
+ * rough part is in their phase). Call after rbx_set_geometry (which resets it to 0); rays
+ * must be traced again. Errors: RBX_EINVAL (mode not 0 or 1), RBX_ESTATE. */
+rbx_status rbx_set_integration(rbx_job *job, int mode);
+
+/* One update from a set of nf frequencies (Sec. 6.3.2: the paper takes two consecutive
+ * frequencies per update). The rays are traced once, on the map smoothed (and, when lossy,
+ * dispersed) for freqs[0]; each frequency contributes its own residual and preconditioned
+ * back-projection, and the search directions are summed before one step m <- m + tau dm.
+ * data_dev: nf consecutive N x N complex64 blocks (device, emitter-major). nf == 1 is
+ * rbx_update_frequency. out->resid_norm2 is summed over the set (no per-stage timings).
+ * Synchronises. Errors: RBX_EINVAL (nf < 1 or > 16, bad frequencies), RBX_ESTATE, RBX_ENOMEM,
+ * RBX_ENUMERIC as rbx_update_frequency. */
+rbx_status rbx_update_set(rbx_job *job, const double *freqs_hz, int nf, double dfreq_hz, const void *data_dev,
+                          rbx_stats *out);
+
 /* Copy the job's current sound-speed map out (ny*nx float32, device). */
 rbx_status rbx_get_model(rbx_job *job, float *c_dev);
 

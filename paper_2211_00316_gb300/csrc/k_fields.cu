@@ -119,8 +119,11 @@ __global__ void k_smooth_y_map(const double *__restrict__ t, double *__restrict_
 // smoothed 1/c. Lossy (as != nullptr): n_e = smoothed 1/c + tn * smoothed alpha0 with
 // tn = tan(pi y/2) omega^(y-1) (the box filter is linear, so this is the smoothed real
 // wavenumber map over omega), and the record's slot 6 holds alpha = wy * smoothed alpha0.
+// Integration on the non-smoothed map (c_raw != nullptr): slot 7 holds the non-smoothed
+// slowness 1/c (+ tn alpha0 when lossy) and slot 6 the non-smoothed alpha.
 __global__ void k_fields(const double *__restrict__ ns, const double *__restrict__ as, double tn, double wy,
-                         float *__restrict__ F, int nx, int ny, double dx)
+                         const float *__restrict__ c_raw, const float *__restrict__ a_raw, float *__restrict__ F,
+                         int nx, int ny, double dx)
 {
     int ix = blockIdx.x * blockDim.x + threadIdx.x, iy = blockIdx.y;
     if (ix >= nx) return;
@@ -134,14 +137,20 @@ __global__ void k_fields(const double *__restrict__ ns, const double *__restrict
     double fxx = (at(ix + 1, iy) - 2 * c + at(ix - 1, iy)) / (dx * dx);
     double fxy = (at(ix + 1, iy + 1) - at(ix - 1, iy + 1) - at(ix + 1, iy - 1) + at(ix - 1, iy - 1)) / (4 * dx * dx);
     double fyy = (at(ix, iy + 1) - 2 * c + at(ix, iy - 1)) / (dx * dx);
-    const float al = as ? (float)(wy * as[(size_t)iy * nx + ix]) : 0.f;
-    float4 *o = reinterpret_cast<float4 *>(F + (size_t)(iy * nx + ix) * kFieldStride);
+    const size_t k0 = (size_t)iy * nx + ix;
+    float al = as ? (float)(wy * as[k0]) : 0.f, nr = 0.f;
+    if (c_raw) {
+        const double a0 = a_raw ? (double)a_raw[k0] : 0.0;
+        nr = (float)(1.0 / (double)c_raw[k0] + tn * a0);
+        if (as) al = (float)(wy * a0);
+    }
+    float4 *o = reinterpret_cast<float4 *>(F + k0 * kFieldStride);
     o[0] = make_float4((float)c, (float)fx, (float)fy, (float)fxx);
-    o[1] = make_float4((float)fxy, (float)fyy, al, 0.f);
+    o[1] = make_float4((float)fxy, (float)fyy, al, nr);
 }
 
 void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *tmp64, double *ns64, float *ns,
-                          float *fields, const Lossy &ab, double f, cudaStream_t s)
+                          float *fields, const Lossy &ab, double f, bool raw, cudaStream_t s)
 {
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
     k_smooth_x<<<grd, blk, 0, s>>>(c, tmp64, g.nx, g.ny, w);
@@ -154,7 +163,8 @@ void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *
         k_smooth_x_map<<<grd, blk, 0, s>>>(ab.alpha0, tmp64, g.nx, g.ny, w);
         k_smooth_y_map<<<grd, blk, 0, s>>>(tmp64, ab.as64, g.nx, g.ny, w);
     }
-    k_fields<<<grd, blk, 0, s>>>(ns64, ab.alpha0 ? ab.as64 : nullptr, tn, wy, fields, g.nx, g.ny, g.dx);
+    k_fields<<<grd, blk, 0, s>>>(ns64, ab.alpha0 ? ab.as64 : nullptr, tn, wy, raw ? c : nullptr, ab.alpha0, fields, g.nx,
+                                 g.ny, g.dx);
 }
 
 __global__ void k_check_model(const float *c, int n, unsigned long long *flag)

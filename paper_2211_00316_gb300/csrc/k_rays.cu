@@ -26,6 +26,7 @@ __device__ __forceinline__ int clampi_(int i, int lo, int hi) { return i < lo ? 
 
 struct Fv {
     float n, gx, gy, hxx, hxy, hyy, al;   // al: absorption coefficient alpha (lossy media only)
+    float nr;                              // slowness integrated along the ray (n, or the non-smoothed one)
 };
 
 // 1/v for v in the range of a slowness or a triangle's edge sum: the hardware approximation
@@ -46,7 +47,7 @@ __device__ __forceinline__ void kadd(float &s, float &c, float inc)
     s = t;
 }
 
-template <bool LOSSY>
+template <bool LOSSY, bool RAW>
 __device__ __forceinline__ void field_eval(const float *__restrict__ F, const RayParams &p, float px, float py, Fv &o)
 {
     float u = (px - p.x0) * p.inv_dx, v = (py - p.y0) * p.inv_dx;
@@ -64,6 +65,7 @@ __device__ __forceinline__ void field_eval(const float *__restrict__ F, const Ra
     o.hxy = w00 * a1.x + w10 * b1.x + w01 * c1.x + w11 * d1.x;
     o.hyy = w00 * a1.y + w10 * b1.y + w01 * c1.y + w11 * d1.y;
     o.al = LOSSY ? w00 * a1.z + w10 * b1.z + w01 * c1.z + w11 * d1.z : 0.f;
+    o.nr = RAW ? w00 * a1.w + w10 * b1.w + w01 * c1.w + w11 * d1.w : o.n;
 }
 
 // A ray sample as a triangle vertex.
@@ -277,7 +279,7 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
     }
 }
 
-template <bool LOSSY>
+template <bool LOSSY, bool RAW>
 __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict__ F, const int4 *__restrict__ rows_g,
                                                          TabEntry *__restrict__ tab, float4 *__restrict__ exits,
                                                          RayParams p, unsigned long long *counters)
@@ -307,7 +309,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
 
     // reference ray (x, p) and paraxial ray (dx, dp); F1 caches the fields at x
     Fv F1;
-    field_eval<LOSSY>(F, p, x, y, F1);
+    field_eval<LOSSY, RAW>(F, p, x, y, F1);
     float px, py, dpx, dpy, dxx = 0.f, dxy = 0.f, T = 0.f, Tc = 0.f;
     float B = 0.f, Bc = 0.f;   // lossy media: B = int alpha ds by the rule of T; a gains exp(-B)
     // compensation terms of x, p, dx (T has Tc)
@@ -350,14 +352,14 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
             kadd(x, cx, ds * tx); kadd(y, cy, ds * ty);
             kadd(dxx, cdx, ds * (dpx * in)); kadd(dxy, cdy, ds * (dpy * in));
-            kadd(T, Tc, hds * (n + n));
+            kadd(T, Tc, hds * (F1.nr + F1.nr));
             if (LOSSY) kadd(B, Bc, hds * (F1.al + F1.al));
             const float J = dxx * ty - dxy * tx;
-            if (i == 0) { sc1 = sqrtf(n * fabsf(J) / ds); Jlast = J; }
+            if (i == 0) { sc1 = sqrtf(F1.nr * fabsf(J) / ds); Jlast = J; }
             else if (J * Jlast < 0.f) K++;
             if (J != 0.f) Jlast = J;
             cur.x = x; cur.y = y; cur.T = T; cur.kx = tx; cur.ky = ty; cur.K = K;
-            cur.a = sc1 * rsqrtf(n * fabsf(J));
+            cur.a = sc1 * rsqrtf(F1.nr * fabsf(J));
             if (LOSSY) cur.a *= expf(-B);
             have = true;
         } else if (alive) {
@@ -369,7 +371,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             const float qx = px * in, qy = py * in;
             // stage 2 at the auxiliary point x + ds q_x
             Fv F2;
-            field_eval<LOSSY>(F, p, x + ds * qx, y + ds * qy, F2);
+            field_eval<LOSSY, RAW>(F, p, x + ds * qx, y + ds * qy, F2);
             const float na = F2.n, ina = rcp_nr(na);
             float pax = px + ds * F1.gx, pay = py + ds * F1.gy;
             const float sca = na * rsqrtf(pax * pax + pay * pay);
@@ -395,8 +397,8 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             const float ddxx = hds * (qdxx + qdxax), ddxy = hds * (qdxy + qdxay);
             const float ddpx2 = hds * (qdpx + qdpax), ddpy2 = hds * (qdpy + qdpay);
             const float xn = x + ds * dirx, yn = y + ds * diry;
-            field_eval<LOSSY>(F, p, xn, yn, F2);                // fields at the new sample (reused next step)
-            float inc = hds * (n + F2.n), incB = LOSSY ? hds * (F1.al + F2.al) : 0.f;
+            field_eval<LOSSY, RAW>(F, p, xn, yn, F2);                // fields at the new sample (reused next step)
+            float inc = hds * (F1.nr + F2.nr), incB = LOSSY ? hds * (F1.al + F2.al) : 0.f;
             const bool last = xn * xn + yn * yn >= R2;
             if (last) {
                 // final partial step: crossing of the step's chord with the ring; the other
@@ -412,7 +414,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
                 dxx += fr * ddxx; dxy += fr * ddxy;
                 dpx += fr * ddpx2; dpy += fr * ddpy2;
                 px += fr * ddpx; py += fr * ddpy;
-                field_eval<LOSSY>(F, p, x, y, F2);
+                field_eval<LOSSY, RAW>(F, p, x, y, F2);
             } else {
                 kadd(x, cx, ds * dirx); kadd(y, cy, ds * diry);
                 kadd(px, cpx, ddpx); kadd(py, cpy, ddpy);
@@ -424,11 +426,11 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             F1 = F2;
             const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
             const float J = dxx * ty - dxy * tx;
-            if (i == 0) { sc1 = sqrtf(F1.n * fabsf(J) / ds); Jlast = J; }
+            if (i == 0) { sc1 = sqrtf(F1.nr * fabsf(J) / ds); Jlast = J; }
             else if (J * Jlast < 0.f) K++;   // caustic: sign change of the ray Jacobian
             if (J != 0.f) Jlast = J;
             cur.x = x; cur.y = y; cur.T = T; cur.kx = tx; cur.ky = ty; cur.K = K;
-            cur.a = sc1 * rsqrtf(F1.n * fabsf(J));
+            cur.a = sc1 * rsqrtf(F1.nr * fabsf(J));
             if (LOSSY) cur.a *= expf(-B);
             have = true;
             if (last) {
@@ -470,7 +472,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
                 if (lane == 31) okR = true;
                 else if (aR) okR = okR && (x - xr) * (x - xr) + (y - yr) * (y - yr) < gap2;
                 if (out && okL && okR) {
-                    const float n = F1.n, in = rcp_nr(n), inc = hds * (n + n);
+                    const float n = F1.n, in = rcp_nr(n), inc = hds * (F1.nr + F1.nr);
                     const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
                     const float b = x * tx + y * ty, se = -b + sqrtf(fmaxf(b * b - (fmaf(x, x, y * y) - R2), 0.f));
                     const int m = max(0, (int)floorf(se / ds));
@@ -488,10 +490,10 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
                         kadd(B, Bc, (t / ds) * incB);
                     }
                     dxx = fmaf(sm + t, dpx * in, dxx); dxy = fmaf(sm + t, dpy * in, dxy);
-                    field_eval<LOSSY>(F, p, x, y, F1);
+                    field_eval<LOSSY, RAW>(F, p, x, y, F1);
                     const float J = dxx * ty - dxy * tx;
                     if (J * Jlast < 0.f) K++;
-                    const float a = sc1 * rsqrtf(F1.n * fabsf(J)) * (LOSSY ? expf(-B) : 1.f);
+                    const float a = sc1 * rsqrtf(F1.nr * fabsf(J)) * (LOSSY ? expf(-B) : 1.f);
                     if (lane < 31 || j == N - 1)
                         exits[(size_t)e * (N - 1) + (j - 1)] = make_float4(atan2f(y, x), T, a, (float)K);
                     alive = false;
@@ -506,7 +508,8 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
 }
 
 // Largest radius of a node whose fields differ from the uniform medium of node (0, 0)
-// (n and alpha there, all derivatives zero); +inf when node (0, 0) itself is not uniform.
+// (n, alpha and the integrated slowness there, all derivatives zero); +inf when node (0, 0)
+// itself is not uniform.
 __global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsigned long long *ru)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -517,7 +520,7 @@ __global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsi
         return;
     }
     const bool uni = a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f &&
-                     a1.z == u1.z;
+                     a1.z == u1.z && a1.w == u1.w;
     if (!uni) {
         const float px = p.x0 + (float)(k % p.nx) * p.dx, py = p.y0 + (float)(k / p.nx) * p.dx;
         atomicMax(ru, (unsigned long long)__float_as_uint(sqrtf(px * px + py * py)));
@@ -531,14 +534,19 @@ void launch_uniform_radius(const float *fields, const RayParams &p, unsigned lon
 }
 
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
-                         unsigned long long *counters, bool lossy, cudaStream_t s)
+                         unsigned long long *counters, bool lossy, bool raw, cudaStream_t s)
 {
     int nwarps = (p.N - 2 + 30) / 31;
     dim3 grd((nwarps + 3) / 4, p.N);
-    if (lossy)
-        k_trace_raster<true><<<grd, 128, (size_t)p.ny * sizeof(int4), s>>>(fields, rows, tab, exits, p, counters);
+    const size_t sm = (size_t)p.ny * sizeof(int4);
+    if (lossy && raw)
+        k_trace_raster<true, true><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
+    else if (lossy)
+        k_trace_raster<true, false><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
+    else if (raw)
+        k_trace_raster<false, true><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
     else
-        k_trace_raster<false><<<grd, 128, (size_t)p.ny * sizeof(int4), s>>>(fields, rows, tab, exits, p, counters);
+        k_trace_raster<false, false><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
 }
 
 // rows[iy] = (compact index of the row's first mask node, first ix, last ix); empty rows

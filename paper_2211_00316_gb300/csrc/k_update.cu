@@ -155,7 +155,8 @@ __global__ __launch_bounds__(RB) void k_update(const float2 *__restrict__ gpart,
                                                int nxy, float sgn, double pref_over_w, double tau, float c0,
                                                float *__restrict__ c, double *__restrict__ red,
                                                unsigned long long *counters, const float *__restrict__ alpha0,
-                                               double w, double y, double wy, double tn)
+                                               double w, double y, double wy, double tn, double *__restrict__ acc,
+                                               int mode)
 {
     __shared__ double sh[RB];
     int k = blockIdx.x * RB + threadIdx.x;
@@ -180,17 +181,25 @@ __global__ __launch_bounds__(RB) void k_update(const float2 *__restrict__ gpart,
             } else {
                 dm = -pref_over_w * m * grad;
             }
-            double mn = m + tau * dm;
-            if (!(mn > 0.0) || !isfinite(mn)) {
-                atomicAdd(&counters[4], 1ull);
-                mn = m;
+            // frequency sets: mode 1 starts the sum of the set's search directions, mode 2 adds
+            // to it (the model is not touched), mode 3 adds the last one and applies the step;
+            // mode 0 is a single frequency
+            if (mode == 1 || mode == 2) {
+                acc[xi] = (mode == 1 ? 0.0 : acc[xi]) + dm;
+            } else {
+                if (mode == 3) dm += acc[xi];
+                double mn = m + tau * dm;
+                if (!(mn > 0.0) || !isfinite(mn)) {
+                    atomicAdd(&counters[4], 1ull);
+                    mn = m;
+                }
+                float cn = (float)(1.0 / sqrt(mn));
+                c[k] = cn;
+                double dc = (double)cn - cold;
+                dc2 = dc * dc;
+                dcm = fabs(dc);
+                dm2 = dm * dm;
             }
-            float cn = (float)(1.0 / sqrt(mn));
-            c[k] = cn;
-            double dc = (double)cn - cold;
-            dc2 = dc * dc;
-            dcm = fabs(dc);
-            dm2 = dm * dm;
         }
     }
     double s1 = block_sum(dc2, sh), s2 = block_max(dcm, sh), s3 = block_sum(dm2, sh);
@@ -218,7 +227,7 @@ __global__ void k_final_update(const double *__restrict__ red, int nb, double *_
 
 void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X, int weight_mode, double f,
                    double df, double tau, double c0, float *c, double *red, unsigned long long *counters,
-                   const Lossy &ab, cudaStream_t s)
+                   const Lossy &ab, double *acc, int mode, cudaStream_t s)
 {
     const double PI = 3.14159265358979323846;
     double w = 2 * PI * f, dw = 2 * PI * df;
@@ -226,7 +235,7 @@ void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X
     int nb = update_blocks(nx, ny);
     const double wy = ab.alpha0 ? pow(w, ab.y) : 0.0, tn = ab.alpha0 ? tan(PI * ab.y / 2) : 0.0;
     k_update<<<nb, RB, 0, s>>>(gpart, node2x, X, nx * ny, weight_mode == 0 ? -1.f : 1.f, pref / w, tau, (float)c0, c,
-                               red, counters, ab.alpha0, w, ab.y, wy, tn);
+                               red, counters, ab.alpha0, w, ab.y, wy, tn, acc, mode);
     k_final_update<<<1, 32, 0, s>>>(red, nb, red + 3 * nb);
 }
 
@@ -272,6 +281,17 @@ void launch_snapshot(const double *r2, const double *upd3, const unsigned long l
                      double *slot, cudaStream_t s)
 {
     k_snapshot<<<1, 32, 0, s>>>(r2, upd3, counters, tc_err, slot);
+}
+
+// dst = (first ? 0 : dst) + src: the residual norm summed over a frequency set
+__global__ void k_acc_scalar(const double *__restrict__ src, double *__restrict__ dst, int first)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) dst[0] = (first ? 0.0 : dst[0]) + src[0];
+}
+
+void launch_acc_scalar(const double *src, double *dst, bool first, cudaStream_t s)
+{
+    k_acc_scalar<<<1, 32, 0, s>>>(src, dst, first ? 1 : 0);
 }
 
 }  // namespace rbx

@@ -26,6 +26,7 @@ struct rbx_job {
     int ns_window = 0;
     double ns_freq = 0.0;      // frequency the fields were made for (lossy fields depend on it)
     bool lossy = false;        // absorption map set (rbx_set_absorption)
+    bool raw = false;          // integration on the non-smoothed map (rbx_set_integration)
     double abs_y = 0.0;
     Workspace w;
     int *d_count = nullptr;
@@ -86,7 +87,8 @@ static cudaError_t dalloc(T *&p, size_t n, cudaStream_t s)
 static void free_ws(Workspace &w, cudaStream_t s)
 {
     void *ps[] = {w.hist, w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
-                  w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters, w.alpha0, w.as64};
+                  w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters, w.alpha0, w.as64,
+                  w.dmacc};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, s);
     tc_free(w.tc, s);
@@ -184,7 +186,7 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     free_ws(j->w, j->stream);
     keep_pool_memory();
-    j->has_geom = j->has_tables = j->ns_valid = j->lossy = false;
+    j->has_geom = j->has_tables = j->ns_valid = j->lossy = j->raw = false;
     Workspace &w = j->w;
     w.N = g.n_xducers;
     w.nx = g.nx;
@@ -344,7 +346,8 @@ static rbx_status smooth(rbx_job *j, double f)
 {
     int w = window_for(f, j->g.dx);
     if (j->ns_valid && j->ns_window == w && (!j->lossy || j->ns_freq == f)) return RBX_OK;
-    launch_smooth_fields(j->g, j->w.c, w, j->w.tmp64, j->w.ns64, j->w.ns, j->w.fields, lossy_of(j), f, j->stream);
+    launch_smooth_fields(j->g, j->w.c, w, j->w.tmp64, j->w.ns64, j->w.ns, j->w.fields, lossy_of(j), f, j->raw,
+                         j->stream);
     LAUNCHED(j, j->lossy ? 5 : 3);
     j->ns_valid = true;
     j->ns_window = w;
@@ -375,7 +378,7 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     p.maxs = max_steps(j->g);
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
     launch_uniform_radius(w.fields, p, w.counters + 7, j->stream);
-    launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->lossy, j->stream);
+    launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->lossy, j->raw, j->stream);
     LAUNCHED(j, 2);
     if ((st = record(j, EV_TRACE))) return st;
     launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
@@ -476,9 +479,15 @@ rbx_status rbx_predict(rbx_job *j, double f, void *g_dev)
     rbx_status st;
     if ((st = smooth(j, f))) return st;
     launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
-    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
-    LAUNCHED(j, 2);
-    if ((st = forward_core(j, f, false))) return st;
+    LAUNCHED(j, 1);
+    if (j->raw) {
+        // integration on the non-smoothed map: the ray Green's function alone (Sec. 6.3.2)
+        CUDA_TRY(j, cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)w.N * w.N, j->stream));
+    } else {
+        launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
+        LAUNCHED(j, 1);
+        if ((st = forward_core(j, f, false))) return st;
+    }
     launch_add_offdiag(w.gdir, w.D, w.N, static_cast<float2 *>(g_dev), j->stream);
     LAUNCHED(j, 1);
     return RBX_OK;
@@ -518,19 +527,25 @@ rbx_status rbx_adjoint(rbx_job *j, double f, const void *R_dev, void *out_dev, i
 
 // Steps a5-a9 queued on the job's stream with no host interaction (capturable into a CUDA
 // graph); the update's scalar results are copied into device history slot `slot`.
-static rbx_status enqueue_update(rbx_job *j, double f, double df, const float2 *data, bool traced, int slot)
+// Steps a5-a8 of one frequency f on the current tables and the update kernel in `mode`
+// (0: apply this frequency's step; 1/2/3: start / add to / finish a frequency set's sum).
+static rbx_status enqueue_freq(rbx_job *j, double f, double df, const float2 *data, int mode)
 {
     Workspace &w = j->w;
     rbx_status st;
-    if (!traced && (st = record(j, EV_TABLES))) return st;
-    if ((st = smooth(j, f))) return st;
-    CUDA_TRY(j, cudaMemsetAsync(w.counters + 1, 0, sizeof(unsigned long long), j->stream));
-    CUDA_TRY(j, cudaMemsetAsync(w.counters + 4, 0, sizeof(unsigned long long), j->stream));
     launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
-    launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
-    LAUNCHED(j, 2);
+    LAUNCHED(j, 1);
     if ((st = record(j, EV_GDIR))) return st;
-    if ((st = forward_core(j, f, true))) return st;
+    if (j->raw) {
+        // integration on the non-smoothed map: the residual is the ray Green's function alone
+        CUDA_TRY(j, cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)w.N * w.N, j->stream));
+        if ((st = record(j, EV_SYNTH_F))) return st;
+        if ((st = record(j, EV_GEMM_F))) return st;
+    } else {
+        launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
+        LAUNCHED(j, 1);
+        if ((st = forward_core(j, f, true))) return st;
+    }
     launch_residual(w.gdir, w.D, data, w.N, nullptr, w.Rs, w.red, j->stream);
     LAUNCHED(j, 2);
     if ((st = record(j, EV_RESID))) return st;
@@ -550,10 +565,24 @@ static rbx_status enqueue_update(rbx_job *j, double f, double df, const float2 *
     if ((st = record(j, EV_GEMM_B))) return st;
     const int roff = residual_blocks(w.N) + 8;
     launch_update(w.gpart, w.node2x, w.nx, w.ny, w.X, j->g.weight_mode, f, df, j->g.tau, j->g.c0, w.c, w.red + roff,
-                  w.counters, lossy_of(j), j->stream);
+                  w.counters, lossy_of(j), w.dmacc, mode, j->stream);
+    LAUNCHED(j, 2);
+    return RBX_OK;
+}
+
+static rbx_status enqueue_update(rbx_job *j, double f, double df, const float2 *data, bool traced, int slot)
+{
+    Workspace &w = j->w;
+    rbx_status st;
+    if (!traced && (st = record(j, EV_TABLES))) return st;
+    if ((st = smooth(j, f))) return st;
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 1, 0, sizeof(unsigned long long), j->stream));
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 4, 0, sizeof(unsigned long long), j->stream));
+    if ((st = enqueue_freq(j, f, df, data, 0))) return st;
+    const int roff = residual_blocks(w.N) + 8;
     launch_snapshot(w.red + residual_blocks(w.N), w.red + roff + 3 * update_blocks(w.nx, w.ny), w.counters,
                     w.tc.err, w.hist + (size_t)slot * kHistStride, j->stream);
-    LAUNCHED(j, 3);
+    LAUNCHED(j, 1);
     if ((st = record(j, EV_UPDATE))) return st;
     j->ns_valid = false;   // the model changed
     return RBX_OK;
@@ -653,6 +682,53 @@ rbx_status rbx_update_frequency(rbx_job *j, double f, double df, const void *dat
     rbx_status st = rbx_trace_rays(j, f);
     if (st) return st;
     st = update_core(j, f, df, static_cast<const float2 *>(data_dev), out, true);
+    if (out) out->n_launches = j->launches - l0;
+    return st;
+}
+
+rbx_status rbx_set_integration(rbx_job *j, int mode)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_set_integration before rbx_set_geometry");
+    NEED(j, mode == 0 || mode == 1, RBX_EINVAL, "integration mode must be 0 (smoothed) or 1 (non-smoothed)");
+    j->raw = mode == 1;
+    j->ns_valid = j->has_tables = false;
+    return RBX_OK;
+}
+
+rbx_status rbx_update_set(rbx_job *j, const double *freqs, int nf, double df, const void *data_dev, rbx_stats *out)
+{
+    if (!j || !freqs || !data_dev || nf < 1) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_update_set before rbx_set_geometry");
+    NEED(j, nf <= 16, RBX_EINVAL, "at most 16 frequencies per set");
+    NEED(j, std::isfinite(df) && df > 0, RBX_EINVAL, "frequency spacing must be finite and > 0");
+    for (int k = 0; k < nf; k++) NEED(j, !bad_freq(freqs[k]), RBX_EINVAL, "frequencies must be finite and > 0");
+    if (nf == 1) return rbx_update_frequency(j, freqs[0], df, data_dev, out);
+    Workspace &w = j->w;
+    long long l0 = j->launches;
+    if (!w.dmacc && dalloc(w.dmacc, (size_t)w.X, j->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(j, RBX_ENOMEM, "device allocation of the set accumulator failed");
+    }
+    // one trace for the set, on the map smoothed (and dispersed) for its first frequency
+    rbx_status st = rbx_trace_rays(j, freqs[0]);
+    if (st) return st;
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 1, 0, sizeof(unsigned long long), j->stream));
+    CUDA_TRY(j, cudaMemsetAsync(w.counters + 4, 0, sizeof(unsigned long long), j->stream));
+    const size_t nn = (size_t)w.N * w.N;
+    const int nb = residual_blocks(w.N), roff = nb + 8;
+    for (int k = 0; k < nf; k++) {
+        const float2 *d = static_cast<const float2 *>(data_dev) + (size_t)k * nn;
+        if ((st = enqueue_freq(j, freqs[k], df, d, k == 0 ? 1 : (k < nf - 1 ? 2 : 3)))) return st;
+        launch_acc_scalar(w.red + nb, w.red + nb + 4, k == 0, j->stream);
+        LAUNCHED(j, 1);
+    }
+    launch_snapshot(w.red + nb + 4, w.red + roff + 3 * update_blocks(w.nx, w.ny), w.counters, w.tc.err, w.hist,
+                    j->stream);
+    LAUNCHED(j, 1);
+    if ((st = record(j, EV_UPDATE))) return st;
+    j->ns_valid = false;
+    st = read_stats(j, 0, out, true, false);
     if (out) out->n_launches = j->launches - l0;
     return st;
 }

@@ -8,7 +8,7 @@
 
 namespace rbx {
 
-constexpr int kFieldStride = 8;          // floats per node: n, n_x, n_y, n_xx, n_xy, n_yy, alpha, 0
+constexpr int kFieldStride = 8;          // floats per node: n, n_x, n_y, n_xx, n_xy, n_yy, alpha, n_raw
 constexpr uint32_t kUncovered = 0xFFFFFFFFu;
 constexpr int kMaxSteps = 2047;          // ray samples index i < 2048 (11 bits of the key)
 constexpr int kMaxXducers = 4095;        // ray index j < 4096 (12 bits of the key)
@@ -63,6 +63,7 @@ struct Workspace {
     float2 *v = nullptr;        // Born weight Upsilon_m dA (m - m_s) per mask node (complex when lossy)
     float *alpha0 = nullptr;    // absorption map alpha0 [ny][nx], Np (rad/s)^-y m^-1 (lossy jobs only)
     double *as64 = nullptr;     // smoothed alpha0 (lossy jobs only)
+    double *dmacc = nullptr;    // sum of a frequency set's search directions per mask node
     float2 *gdir = nullptr, *D = nullptr, *R = nullptr, *Rs = nullptr, *part = nullptr, *gpart = nullptr;
     float2 *data = nullptr;
     double *red = nullptr;           // reduction scratch
@@ -84,7 +85,7 @@ struct Lossy {
     double y = 0.0;
 };
 void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *tmp64, double *ns64, float *ns,
-                          float *fields, const Lossy &ab, double f, cudaStream_t s);
+                          float *fields, const Lossy &ab, double f, bool raw, cudaStream_t s);
 void launch_check_model(const float *c, int n, unsigned long long *flag, cudaStream_t s);
 void launch_check_alpha(const float *a, int n, unsigned long long *flag, cudaStream_t s);
 void launch_fill(float *p, float v, size_t n, cudaStream_t s);
@@ -92,7 +93,7 @@ void launch_fill(float *p, float v, size_t n, cudaStream_t s);
 // k_rays.cu
 void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s);
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
-                         unsigned long long *counters, bool lossy, cudaStream_t s);
+                         unsigned long long *counters, bool lossy, bool raw, cudaStream_t s);
 void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s);
 void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, unsigned long long *counters, cudaStream_t s);
 void launch_direct_green(const float4 *exits, int N, double f, double c0, float2 *g, unsigned long long *counters,
@@ -139,9 +140,10 @@ void launch_combine_adjoint(const float2 *gpart, int X, int mode, int weight_mod
 // plain adjoint of a lossy job: out[x] = dA conj(Upsilon_m[x]) gpart[x]
 void launch_combine_adjoint_lossy(const float2 *gpart, const float *c, const int *idx, int X, double f, double dA,
                                   const Lossy &ab, float2 *out, cudaStream_t s);
+void launch_acc_scalar(const double *src, double *dst, bool first, cudaStream_t s);
 void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X, int weight_mode, double f,
                    double df, double tau, double c0, float *c, double *red, unsigned long long *counters,
-                   const Lossy &ab, cudaStream_t s);
+                   const Lossy &ab, double *acc, int mode, cudaStream_t s);
 void launch_snapshot(const double *r2, const double *upd3, const unsigned long long *counters, const unsigned *tc_err,
                      double *slot, cudaStream_t s);
 int residual_blocks(int N);

@@ -82,6 +82,8 @@ _SIGS = {
     "rbx_server_wait": [_P, C.c_longlong, C.c_double],
     "rbx_server_cancel": [_P, C.c_longlong],
     "rbx_set_absorption": [_P, _P, C.c_double],
+    "rbx_set_integration": [_P, C.c_int],
+    "rbx_update_set": [_P, C.POINTER(C.c_double), C.c_int, C.c_double, _P, C.POINTER(Stats)],
     "rbx_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
     "rbx_server_times": [_P, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -212,6 +214,19 @@ class Job:
             return
         a = alpha0.contiguous().to(torch.float32)
         self._check(self.L.rbx_set_absorption(self.h, _ptr(a), float(y)))
+
+    def set_integration(self, raw: bool):
+        """True: integrate on the non-smoothed map, no Born term (rbx_set_integration mode 1)."""
+        self._check(self.L.rbx_set_integration(self.h, 1 if raw else 0))
+
+    def update_set(self, freqs, df: float, data: torch.Tensor) -> dict:
+        """One update from a frequency set; data [nf][N][N] complex64 on the device."""
+        fr = np.ascontiguousarray(freqs, dtype=np.float64)
+        st = Stats()
+        d = data.contiguous()
+        self._check(self.L.rbx_update_set(self.h, fr.ctypes.data_as(C.POINTER(C.c_double)), len(fr), float(df),
+                                          _ptr(d), C.byref(st)))
+        return st.as_dict()
 
     def get_model(self) -> torch.Tensor:
         out = torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda")
