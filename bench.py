@@ -445,6 +445,10 @@ def main():
     ap.add_argument("--no-serial", action="store_true", help="served form: skip the serial plain FP32 replay")
     ap.add_argument("--absorption", action="store_true",
                     help="lossy medium: breast absorption map 0-1 dB/(MHz^1.4 cm), y = 1.4 (rbx_set_absorption)")
+    ap.add_argument("--integration", default="smoothed", choices=["smoothed", "raw"],
+                    help="raw: integrate on the non-smoothed map, no Born term (rbx_set_integration 1)")
+    ap.add_argument("--set-size", type=int, default=1,
+                    help="frequencies per update (rbx_update_set); value then counts frequencies per second")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="default workload: requests of the short served run reported beside throughput (0 = none)")
     args = ap.parse_args()
@@ -482,10 +486,14 @@ def main():
         N, X = job.N, job.X
         if args.absorption:
             job.set_absorption(torch.tensor(P.absorption_map(w.c_true), dtype=torch.float32, device="cuda"), 1.4)
+        if args.integration == "raw":
+            job.set_integration(True)
+        K = max(1, args.set_size)
         # synthetic data: the library's own ray-Born prediction on the true model + 40 dB noise
         job.set_model(torch.tensor(w.c_true, dtype=torch.float32, device="cuda"))
-        fidx = [k % len(w.freqs) for k in range(total_steps)]
-        uniq = sorted(set(fidx))
+        fidx = [(k * K) % (len(w.freqs) - K + 1) for k in range(total_steps)]
+        fset = [[fidx[k] + q for q in range(K)] for k in range(total_steps)]
+        uniq = sorted(set(q for fs in fset for q in fs))
         data = {}
         for q in uniq:
             f = float(w.freqs[q])
@@ -497,8 +505,15 @@ def main():
         c_init = torch.tensor(w.c_init, dtype=torch.float32, device="cuda")
         job.set_model(c_init)
         df = w.dfreq
+        set_data = {k: torch.stack([data_dev[q] for q in fset[k]]).contiguous() for k in range(total_steps)} if K > 1 else {}
+
+        def one_update(k):
+            if K > 1:
+                return job.update_set([float(w.freqs[q]) for q in fset[k]], df, set_data[k])
+            return job.update_frequency(float(w.freqs[fidx[k]]), df, data_dev[fidx[k]])
+
         for k in range(args.warmup):
-            job.update_frequency(float(w.freqs[fidx[k]]), df, data_dev[fidx[k]])
+            one_update(k)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -508,7 +523,7 @@ def main():
         ev0.record(stream)
         stats = []
         for k in range(args.warmup, total_steps):
-            stats.append(job.update_frequency(float(w.freqs[fidx[k]]), df, data_dev[fidx[k]]))
+            stats.append(one_update(k))
         ev1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
@@ -516,11 +531,11 @@ def main():
         ms = REP.max_over_ranks(ms, "cuda")
         if world > 1:
             dist.barrier()
-        value = REP.aggregate_throughput(world * args.steps, ms / 1e3)
+        value = REP.aggregate_throughput(world * args.steps * K, ms / 1e3)
 
         # end to end through the host-buffer entry point: H2D of the step's data and D2H of the model
         e2e = None
-        if not args.no_e2e:
+        if not args.no_e2e and K == 1:
             job.set_model(c_init)
             c_host = torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory()
             for k in range(min(2, args.warmup)):
@@ -586,6 +601,7 @@ def main():
             "data": "synthetic (library ray-Born prediction on a seeded breast-like phantom + 40 dB noise)",
             "config": {"workload": describe(w), "mask_nodes": X, "precision": args.precision,
                        "absorption": ("breast map 0-1 dB/(MHz^1.4 cm), y=1.4" if args.absorption else "none"),
+                       "integration": args.integration, "frequencies_per_update": K,
                        "l2": "inputs larger than L2 (tables N*X*16 B = %.2f GB)" % (16.0 * N * X / 1e9),
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": int(sum(s["n_launches"] for s in stats)),
