@@ -102,6 +102,9 @@ def _declare(L):
     L.og_predict_ext.restype = None
     L.og_update_set_ext.argtypes = [_G, _D, C.c_int, C.c_double, _D, _D, C.c_double, C.c_int, _D, _D, _D]
     L.og_update_set_ext.restype = C.c_int
+    L.og_direct_green_linked.argtypes = [_G, C.POINTER(OMedium), C.c_double, _D, C.c_int, C.c_double, _D,
+                                         C.POINTER(C.c_long), _D]
+    L.og_direct_green_linked.restype = C.c_long
 
 
 def _d(a):
@@ -251,6 +254,34 @@ class Oracle:
         cl = self.L.og_direct_green(C.byref(self.g), f, _d(exits), _d(out.view(np.float64)))
         return out, int(cl)
 
+    def direct_green_linked(self, f: float, f6, exits, al=None, nr=None, maxit: int = 8, tol: float = 1e-6,
+                            linear=None):
+        """Direct Green's function on secant-linked rays (linear: analytic c1 + gx x + gy y medium)."""
+        g = self.geom
+        keep = []
+        if linear is not None:
+            c1, gx, gy = linear
+            med = OMedium(1, g.nx, g.ny, g.dx, g.x0, g.y0, None, c1, gx, gy, None, None)
+        else:
+            f6 = _f64(f6)
+            keep.append(f6)
+            ptrs = []
+            for arr in (al, nr):
+                if arr is None:
+                    ptrs.append(None)
+                else:
+                    arr = _f64(arr)
+                    keep.append(arr)
+                    ptrs.append(_d(arr))
+            med = OMedium(0, g.nx, g.ny, g.dx, g.x0, g.y0, _d(f6), 0.0, 0.0, 0.0, ptrs[0], ptrs[1])
+        exits = _f64(exits)
+        out = np.zeros((self.N, self.N), np.complex128)
+        Tl = np.zeros((self.N, self.N))
+        unc = C.c_long(0)
+        cl = self.L.og_direct_green_linked(C.byref(self.g), C.byref(med), f, _d(exits), maxit, tol,
+                                           _d(out.view(np.float64)), C.byref(unc), _d(Tl))
+        return out, int(cl), int(unc.value), Tl
+
     # a7
     def forward(self, f: float, T, a, K, v):
         """D[e, r] = sum_x G_r G_e v (v already includes omega^2 dA)."""
@@ -328,17 +359,19 @@ class Oracle:
         bad = self.L.og_update_frequency_abs(C.byref(self.g), f, df, _d(c), _d(a0), y, _d(dataf), _d(out), _d(st))
         return out, st, bad
 
-    def predict_ext(self, f: float, c, alpha0=None, y: float = 1.4, raw: bool = False):
-        """Predicted data; raw: integration on the non-smoothed map, no Born term (Sec. 6.3.2)."""
+    def predict_ext(self, f: float, c, alpha0=None, y: float = 1.4, raw: bool = False, link: bool = False):
+        """Predicted data; raw: integration on the non-smoothed map, no Born term (Sec. 6.3.2);
+        link: direct Green's function on secant-linked rays."""
         c = _f64(c)
         a0 = None if alpha0 is None else _f64(alpha0)
         out = np.zeros((self.N, self.N), np.complex128)
         st = np.zeros(3)
-        self.L.og_predict_ext(C.byref(self.g), f, _d(c), None if a0 is None else _d(a0), y, int(raw),
-                              _d(out.view(np.float64)), _d(st))
+        self.L.og_predict_ext(C.byref(self.g), f, _d(c), None if a0 is None else _d(a0), y,
+                              int(raw) | (2 if link else 0), _d(out.view(np.float64)), _d(st))
         return out, st
 
-    def update_set(self, freqs, df: float, c, data, alpha0=None, y: float = 1.4, raw: bool = False):
+    def update_set(self, freqs, df: float, c, data, alpha0=None, y: float = 1.4, raw: bool = False,
+                   link: bool = False):
         """One update from a frequency set (data: [nf][N][N])."""
         fr = np.ascontiguousarray(freqs, dtype=np.float64)
         c = _f64(c)
@@ -347,7 +380,7 @@ class Oracle:
         out = np.zeros_like(c)
         st = np.zeros(7)
         bad = self.L.og_update_set_ext(C.byref(self.g), _d(fr), len(fr), df, _d(c), None if a0 is None else _d(a0),
-                                       y, int(raw), _d(dataf), _d(out), _d(st))
+                                       y, int(raw) | (2 if link else 0), _d(dataf), _d(out), _d(st))
         return out, st, bad
 
     def predict(self, f: float, c):

@@ -605,6 +605,84 @@ long og_direct_green(const og_geom *g, double f, const double *exits_all, double
     return clamped;
 }
 
+/* Ray linking (Sec. 4.4; Sec. 6.3.2: the secant method on the initial direction of each
+ * emitter-receiver pair until the ray meets the receiver within a tolerance). The two fan
+ * rays whose exits bracket beta_r (the pair og_direct_green interpolates between) start the
+ * secant iteration on the exit angle; it stops when the exit lies within tol_rad of beta_r
+ * (or after maxit rays), and T, a are then interpolated linearly in exit angle between the
+ * last two rays to beta_r exactly (K from the nearer). Without a bracket the nearest fan ray
+ * is used, as in og_direct_green. Returns the number of such clamped pairs; *unconverged
+ * counts pairs that stopped on maxit; T_out (nullable) receives the linked travel times. */
+long og_direct_green_linked(const og_geom *g, const og_medium *med, double f, const double *exits_all, int maxit,
+                            double tol_rad, double *out, long *unconverged, double *T_out)
+{
+    int N = g->N, maxs = (int)ceil(3.0 * g->R / g->ds) + 8;
+    double w = 2 * M_PI * f, C = 1.0 / sqrt(8 * M_PI * w / g->c0);
+    long clamped = 0, unconv = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : clamped, unconv)
+    for (int e = 0; e < N; e++) {
+        const double *ex = exits_all + (size_t)e * (N - 1) * 4;
+        double be = 2 * M_PI * e / N, xe = g->R * cos(be), ye = g->R * sin(be);
+        osample *buf = malloc(sizeof(osample) * (maxs + 1));
+        for (int r = 0; r < N; r++) {
+            double *o = out + 2 * ((size_t)e * N + r);
+            if (r == e) { o[0] = o[1] = 0; continue; }
+            double t = wrap2pi(2 * M_PI * r / N - be);
+            int found = -1;
+            for (int j = 1; j <= N - 2; j++) {
+                double tj = wrap2pi(ex[(j - 1) * 4] - be), tk = wrap2pi(ex[j * 4] - be);
+                if (tj == tk) continue;
+                if ((tj <= t && t <= tk) || (tk <= t && t <= tj)) { found = j; break; }
+            }
+            double T, a;
+            int K;
+            if (found < 0) {
+                int best = 1;
+                double bd = 1e300;
+                for (int j = 1; j <= N - 1; j++) {
+                    double d = fabs(wrap2pi(ex[(j - 1) * 4] - be) - t);
+                    if (d < bd) { bd = d; best = j; }
+                }
+                const double *A = ex + (best - 1) * 4;
+                T = A[1]; a = A[2]; K = (int)A[3];
+                clamped++;
+            } else {
+                /* secant iterates: (initial angle, exit angle - t, T, a, K) */
+                double g0 = be + M_PI / 2 + M_PI * found / N, g1 = be + M_PI / 2 + M_PI * (found + 1) / N;
+                double f0 = wrap2pi(ex[(found - 1) * 4] - be) - t, f1 = wrap2pi(ex[found * 4] - be) - t;
+                double T0 = ex[(found - 1) * 4 + 1], T1 = ex[found * 4 + 1];
+                double a0 = ex[(found - 1) * 4 + 2], a1 = ex[found * 4 + 2];
+                int K0 = (int)ex[(found - 1) * 4 + 3], K1 = (int)ex[found * 4 + 3];
+                int it = 0;
+                while (fabs(f1) > tol_rad && fabs(f0) > tol_rad && it < maxit && f1 != f0) {
+                    double g2 = g1 - f1 * (g1 - g0) / (f1 - f0);
+                    int M = og_trace_ray(med, g->R, g->ds, xe, ye, g2, maxs, buf);
+                    if (M < 0) break;
+                    const osample *L = &buf[M];
+                    double f2 = wrap2pi(atan2(L->y, L->x) - be) - t;
+                    if (f2 > M_PI) f2 -= 2 * M_PI;
+                    if (f2 < -M_PI) f2 += 2 * M_PI;
+                    g0 = g1; f0 = f1; T0 = T1; a0 = a1; K0 = K1;
+                    g1 = g2; f1 = f2; T1 = L->T; a1 = L->a; K1 = L->K;
+                    it++;
+                }
+                if (fabs(f1) > tol_rad && fabs(f0) > tol_rad) unconv++;
+                double fr = (f1 == f0) ? 0.0 : (0.0 - f0) / (f1 - f0);   /* exit angle interpolated to t */
+                T = T0 + fr * (T1 - T0);
+                a = a0 + fr * (a1 - a0);
+                K = fabs(f0) <= fabs(f1) ? K0 : K1;
+            }
+            double ph = w * T - M_PI * K / 2 + M_PI / 4;
+            o[0] = C * a * cos(ph);
+            o[1] = C * a * sin(ph);
+            if (T_out) T_out[(size_t)e * N + r] = T;
+        }
+        free(buf);
+    }
+    if (unconverged) *unconverged = unconv;
+    return clamped;
+}
+
 /* ------------------------------------------------------------------ a6 */
 
 /* G_e[x] = (8 pi omega/c0)^(-1/2) a exp(i[omega T - pi K/2 + pi/4])   (Eq. 2D_greens)
@@ -875,6 +953,7 @@ typedef struct {
     int X;
     int *idx;
     double *f6, *ns, *T, *a, *gam, *dg, *exits;
+    double *al, *nr;          /* the medium's alpha and integrated slowness maps (may be NULL) */
     int *K, *cov;
     long uncovered, bad_rays;
 } og_state;
@@ -907,7 +986,8 @@ static void state_build_abs(const og_geom *g, double f, const double *c, const d
     s->uncovered = og_tables_abs(g, s->f6, as, NULL, g->N, s->T, s->a, s->gam, s->K, s->cov, s->exits,
                                  &s->bad_rays);
     og_dgamma(g, s->X, s->gam, s->cov, s->dg);
-    free(as);
+    s->al = as;
+    s->nr = NULL;
 }
 
 static void state_build(const og_geom *g, double f, const double *c, og_state *s)
@@ -952,14 +1032,28 @@ static void state_build_raw(const og_geom *g, double f, const double *c, const d
     s->uncovered = og_tables_ext(g, s->f6, ar, nr, NULL, g->N, s->T, s->a, s->gam, s->K, s->cov, s->exits,
                                  &s->bad_rays);
     og_dgamma(g, s->X, s->gam, s->cov, s->dg);
-    free(nr);
-    free(ar);
+    s->al = ar;
+    s->nr = nr;
 }
 
 static void state_free(og_state *s)
 {
     free(s->idx); free(s->ns); free(s->f6); free(s->T); free(s->a); free(s->gam); free(s->dg);
-    free(s->K); free(s->cov); free(s->exits);
+    free(s->K); free(s->cov); free(s->exits); free(s->al); free(s->nr);
+}
+
+#define OG_RAW 1    /* integration on the non-smoothed map, no Born term */
+#define OG_LINK 2   /* direct Green's function on secant-linked rays */
+#define OG_LINK_MAXIT 8
+#define OG_LINK_TOL 1e-6
+
+/* Direct Green's function of a built state: fan interpolation, or linked rays (OG_LINK). */
+static long state_direct_green(const og_geom *g, const og_state *s, double f, int opts, double *out)
+{
+    if (!(opts & OG_LINK)) return og_direct_green(g, f, s->exits, out);
+    og_medium med = {0, g->nx, g->ny, g->dx, g->x0, g->y0, s->f6, 0, 0, 0, s->al, s->nr};
+    long unc = 0;
+    return og_direct_green_linked(g, &med, f, s->exits, OG_LINK_MAXIT, OG_LINK_TOL, out, &unc, NULL) + unc;
 }
 
 /* Predicted data g = g_dir + F[m - m_s] on the current model (a5 + a7): the rays are
@@ -1097,22 +1191,41 @@ int og_update_frequency_abs(const og_geom *g, double f, double df, const double 
     return bad;
 }
 
-/* Predicted data with the integration mode of the set update below: raw = 0 is og_predict /
- * og_predict_abs (g_dir + Born term of the rough part); raw = 1 follows Sec. 6.3.2: g at the
- * ray ends with the phase and amplitude integrated on the non-smoothed map and no Born term
- * (the rough part is already in the phase). alpha0 may be NULL (lossless). */
-void og_predict_ext(const og_geom *g, double f, const double *c, const double *alpha0, double y, int raw,
+/* Predicted data. opts = 0 is og_predict / og_predict_abs (g_dir + Born term of the rough part);
+ * OG_RAW follows Sec. 6.3.2: g at the ray ends with the phase and amplitude integrated on the
+ * non-smoothed map and no Born term (the rough part is already in the phase); OG_LINK takes
+ * g_dir on secant-linked rays instead of the fan's exit-angle interpolation. alpha0 may be
+ * NULL (lossless). */
+void og_predict_ext(const og_geom *g, double f, const double *c, const double *alpha0, double y, int opts,
                     double *out, double *stats)
 {
-    if (!raw) {
+    int raw = opts & OG_RAW;
+    if (!raw && !(opts & OG_LINK)) {
         if (alpha0) og_predict_abs(g, f, c, alpha0, y, out, stats);
         else og_predict(g, f, c, out, stats);
         return;
     }
     og_state s;
-    state_build_raw(g, f, c, alpha0, y, &s);
-    long cl = og_direct_green(g, f, s.exits, out);
-    for (int e = 0; e < g->N; e++) out[2 * ((size_t)e * g->N + e)] = out[2 * ((size_t)e * g->N + e) + 1] = 0;
+    if (raw) state_build_raw(g, f, c, alpha0, y, &s);
+    else state_build_abs(g, f, c, alpha0, y, &s);
+    int N = g->N;
+    long cl = state_direct_green(g, &s, f, opts, out);
+    if (!raw) {
+        double w = 2 * M_PI * f, dA = g->dx * g->dx;
+        double *v = malloc(sizeof(double) * 2 * s.X), *D = malloc(sizeof(double) * 2 * (size_t)N * N);
+        for (int q = 0; q < s.X; q++) {
+            int k = s.idx[q];
+            double u[2], d = 1.0 / (c[k] * c[k]) - s.ns[k] * s.ns[k];
+            upsilon(w, c[k], alpha0 ? alpha0[k] : 0.0, alpha0 ? y : 1.0, u);
+            v[2 * q] = u[0] * dA * d;
+            v[2 * q + 1] = u[1] * dA * d;
+        }
+        og_forward_c(g, f, s.X, s.T, s.a, s.K, v, D);
+        for (size_t i = 0; i < 2 * (size_t)N * N; i++) out[i] += D[i];
+        free(v);
+        free(D);
+    }
+    for (int e = 0; e < N; e++) out[2 * ((size_t)e * N + e)] = out[2 * ((size_t)e * N + e) + 1] = 0;
     if (stats) { stats[0] = s.uncovered; stats[1] = s.bad_rays; stats[2] = cl; }
     state_free(&s);
 }
@@ -1122,11 +1235,13 @@ void og_predict_ext(const og_geom *g, double f, const double *c, const double *a
  * dispersed) for the set's first frequency; each frequency f_k of the set contributes its own
  * residual R_k and back-projection, and the search direction is the sum over the set of
  * -(Delta omega/(2 pi)^3) Re{node factor(f_k) grad_k} (Eq. sound_speed_update summed over the
- * set's omega), applied once with the step tau. raw selects the integration of og_predict_ext.
+ * set's omega), applied once with the step tau. opts: OG_RAW (the integration of og_predict_ext)
+ * and OG_LINK (the direct Green's function on linked rays).
  * data: nf complex [N][N] blocks. stats as og_update_frequency, [3] summed over the set. */
 int og_update_set_ext(const og_geom *g, const double *freqs, int nf, double df, const double *c,
-                      const double *alpha0, double y, int raw, const double *data, double *c_out, double *stats)
+                      const double *alpha0, double y, int opts, const double *data, double *c_out, double *stats)
 {
+    int raw = opts & OG_RAW;
     og_state s;
     if (raw) state_build_raw(g, freqs[0], c, alpha0, y, &s);
     else state_build_abs(g, freqs[0], c, alpha0, y, &s);
@@ -1142,7 +1257,7 @@ int og_update_set_ext(const og_geom *g, const double *freqs, int nf, double df, 
     long cl = 0;
     for (int kf = 0; kf < nf; kf++) {
         double f = freqs[kf], w = 2 * M_PI * f;
-        cl = og_direct_green(g, f, s.exits, R);
+        cl = state_direct_green(g, &s, f, opts, R);
         if (!raw) {
             for (int q = 0; q < s.X; q++) {
                 int k = s.idx[q];

@@ -175,3 +175,77 @@ def test_raw_fixed_point_and_sign(oracle_mod):
     d_est, d_true = (c_out - C0)[m], (ct - C0)[m]
     assert np.dot(d_est, d_true) / np.linalg.norm(d_est) / np.linalg.norm(d_true) > 0.5
     assert d_est[np.argmin(d_true)] < 0
+
+
+# --------------------------------------------------------------- ray linking
+
+
+def _lin_T(c1, g, p, q):
+    """Travel time in c = c1 + g y between points p and q (linear-velocity medium, closed form)."""
+    cp, cq = c1 + g * p[1], c1 + g * q[1]
+    rho2 = (p[0] - q[0]) ** 2 + (p[1] - q[1]) ** 2
+    return np.arccosh(1 + g * g * rho2 / (2 * cp * cq)) / abs(g)
+
+
+def _fan_exits(o, g, e, linear):
+    """Exits (angle, T, a, K) of fan e's rays in an analytic medium, traced one by one."""
+    N = g.n_xducers
+    xe = xducer(g, e)
+    out = np.zeros((N - 1, 4))
+    for j in range(1, N):
+        gam0 = 2 * math.pi * e / N + math.pi / 2 + math.pi * j / N
+        rows = o.trace_ray(xe[0], xe[1], gam0, linear=linear)
+        L = rows[-1]
+        out[j - 1] = (math.atan2(L[1], L[0]), L[2], L[4], L[6])
+    return out
+
+
+def test_linked_rays_meet_the_closed_form_travel_time(oracle_mod):
+    """Sec. 4.4 / 6.3.2 ray linking by the secant method: in the linear-velocity medium
+    c = c1 + g y (bent rays; the water fan misses the receivers) the linked travel time between
+    emitter and receiver equals the arccosh closed form within the integrator's error, and is
+    much closer to it than the fan's exit-angle interpolation."""
+    g = ring_geom()
+    o = oracle_mod.Oracle(g)
+    lin = (1500.0, 0.0, 2000.0)
+    N = g.n_xducers
+    fans = [0, 9, 21, 40]
+    exits = np.zeros((N, N - 1, 4))
+    for e in fans:
+        exits[e] = _fan_exits(o, g, e, lin)
+    f = 1e4
+    gl, cl, unc, Tl = o.direct_green_linked(f, None, exits, linear=lin)
+    assert unc == 0
+    gi, _ = o.direct_green(f, exits)
+    worst_link, worst_interp = 0.0, 0.0
+    for e in fans:
+        for r in range(N):
+            if r == e or abs(((r - e + N // 2) % N) - N // 2) <= 1:
+                continue                           # neighbours: grazing, outside the fan's bracket
+            ref = _lin_T(1500.0, 2000.0, xducer(g, e), xducer(g, r))
+            worst_link = max(worst_link, abs(Tl[e, r] - ref))
+            w = 2 * math.pi * f
+            ti = (np.angle(gi[e, r] * np.exp(-1j * (w * ref + math.pi / 4)))) / w   # interpolated T - ref
+            worst_interp = max(worst_interp, abs(ti))
+    assert worst_link <= 1e-10
+    assert worst_interp > 10 * worst_link
+
+
+def test_linking_in_water_is_the_closed_form(oracle_mod):
+    """In water the linked rays are the straight chords: g = App. B's g0 exactly."""
+    g = ring_geom()
+    o = oracle_mod.Oracle(g)
+    ns, f6 = o.fields_for(np.full((g.ny, g.nx), C0), 3e5)
+    tb = o.tables(f6)
+    f = 3e5
+    gl, cl, unc, Tl = o.direct_green_linked(f, f6, tb.exits)
+    assert unc == 0
+    k = 2 * math.pi * f / C0
+    N = g.n_xducers
+    for e in range(0, N, 5):
+        for r in range(N):
+            if r == e:
+                continue
+            s = np.linalg.norm(xducer(g, e) - xducer(g, r))
+            ref = (8 * math.pi * k * s) ** -0.5 * np.exp(1j * (k * s + math.pi / 4))
+            assert abs(gl[e, r] - ref) <= 1e-9 * abs(ref)
