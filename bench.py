@@ -447,6 +447,8 @@ def main():
                     help="lossy medium: breast absorption map 0-1 dB/(MHz^1.4 cm), y = 1.4 (rbx_set_absorption)")
     ap.add_argument("--integration", default="smoothed", choices=["smoothed", "raw"],
                     help="raw: integrate on the non-smoothed map, no Born term (rbx_set_integration 1)")
+    ap.add_argument("--link", type=int, default=0,
+                    help="secant ray linking of the direct term, new rays per pair (rbx_set_linking; 0: off)")
     ap.add_argument("--set-size", type=int, default=1,
                     help="frequencies per update (rbx_update_set); value then counts frequencies per second")
     ap.add_argument("--serve-requests", type=int, default=48,
@@ -488,6 +490,8 @@ def main():
             job.set_absorption(torch.tensor(P.absorption_map(w.c_true), dtype=torch.float32, device="cuda"), 1.4)
         if args.integration == "raw":
             job.set_integration(True)
+        if args.link > 0:
+            job.set_linking(args.link)
         K = max(1, args.set_size)
         # synthetic data: the library's own ray-Born prediction on the true model + 40 dB noise
         job.set_model(torch.tensor(w.c_true, dtype=torch.float32, device="cuda"))
@@ -601,7 +605,7 @@ def main():
             "data": "synthetic (library ray-Born prediction on a seeded breast-like phantom + 40 dB noise)",
             "config": {"workload": describe(w), "mask_nodes": X, "precision": args.precision,
                        "absorption": ("breast map 0-1 dB/(MHz^1.4 cm), y=1.4" if args.absorption else "none"),
-                       "integration": args.integration, "frequencies_per_update": K,
+                       "integration": args.integration, "frequencies_per_update": K, "linking": args.link,
                        "l2": "inputs larger than L2 (tables N*X*16 B = %.2f GB)" % (16.0 * N * X / 1e9),
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": int(sum(s["n_launches"] for s in stats)),

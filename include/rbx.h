@@ -128,6 +128,16 @@ rbx_status rbx_set_absorption(rbx_job *job, const float *alpha0_dev, double y);
  * must be traced again. Errors: RBX_EINVAL (mode not 0 or 1), RBX_ESTATE. */
 rbx_status rbx_set_integration(rbx_job *job, int mode);
 
+/* Ray linking of the direct term (Sec. 4.4, Sec. 6.3.2): max_rays > 0 links every emitter-
+ * receiver pair by the secant method on the initial angle, started from the two fan rays whose
+ * exits bracket the receiver and kept inside that bracket (regula falsi with the Illinois
+ * weighting), until the exit lies within 1e-6 rad of it or max_rays new rays were traced; T and a are then interpolated in exit angle to the receiver exactly. The rays
+ * follow the job's current smoothed map, integration mode and absorption. 0 (default): the
+ * fan's exit-angle interpolation (one secant step's worth of accuracy). Applies to
+ * rbx_direct_green, rbx_predict and every update. Pairs left unbracketed or unconverged are
+ * counted in rbx_stats.n_clamped. Errors: RBX_EINVAL (max_rays < 0 or > 32), RBX_ESTATE. */
+rbx_status rbx_set_linking(rbx_job *job, int max_rays);
+
 /* One update from a set of nf frequencies (Sec. 6.3.2: the paper takes two consecutive
  * frequencies per update). The rays are traced once, on the map smoothed (and, when lossy,
  * dispersed) for freqs[0]; each frequency contributes its own residual and preconditioned

@@ -608,10 +608,11 @@ long og_direct_green(const og_geom *g, double f, const double *exits_all, double
 /* Ray linking (Sec. 4.4; Sec. 6.3.2: the secant method on the initial direction of each
  * emitter-receiver pair until the ray meets the receiver within a tolerance). The two fan
  * rays whose exits bracket beta_r (the pair og_direct_green interpolates between) start the
- * secant iteration on the exit angle; it stops when the exit lies within tol_rad of beta_r
- * (or after maxit rays), and T, a are then interpolated linearly in exit angle between the
- * last two rays to beta_r exactly (K from the nearer). Without a bracket the nearest fan ray
- * is used, as in og_direct_green. Returns the number of such clamped pairs; *unconverged
+ * secant iteration on the exit angle, kept inside the bracket (regula falsi with the Illinois
+ * weighting, so no ray leaves the fan's inward directions); it stops when the exit lies within
+ * tol_rad of beta_r (or after maxit rays), and T, a are then interpolated linearly in exit
+ * angle between the two bracketing rays to beta_r exactly (K from the nearer). Without a
+ * bracket the nearest fan ray is used, as in og_direct_green. Returns the number of such clamped pairs; *unconverged
  * counts pairs that stopped on maxit; T_out (nullable) receives the linked travel times. */
 long og_direct_green_linked(const og_geom *g, const og_medium *med, double f, const double *exits_all, int maxit,
                             double tol_rad, double *out, long *unconverged, double *T_out)
@@ -647,30 +648,41 @@ long og_direct_green_linked(const og_geom *g, const og_medium *med, double f, co
                 T = A[1]; a = A[2]; K = (int)A[3];
                 clamped++;
             } else {
-                /* secant iterates: (initial angle, exit angle - t, T, a, K) */
-                double g0 = be + M_PI / 2 + M_PI * found / N, g1 = be + M_PI / 2 + M_PI * (found + 1) / N;
-                double f0 = wrap2pi(ex[(found - 1) * 4] - be) - t, f1 = wrap2pi(ex[found * 4] - be) - t;
-                double T0 = ex[(found - 1) * 4 + 1], T1 = ex[found * 4 + 1];
-                double a0 = ex[(found - 1) * 4 + 2], a1 = ex[found * 4 + 2];
-                int K0 = (int)ex[(found - 1) * 4 + 3], K1 = (int)ex[found * 4 + 3];
-                int it = 0;
-                while (fabs(f1) > tol_rad && fabs(f0) > tol_rad && it < maxit && f1 != f0) {
-                    double g2 = g1 - f1 * (g1 - g0) / (f1 - f0);
-                    int M = og_trace_ray(med, g->R, g->ds, xe, ye, g2, maxs, buf);
+                /* bracketing secant (regula falsi, Illinois): a and b always bracket the
+                 * receiver's exit angle, so every new ray starts strictly between the two fan
+                 * rays (inward) and the exit angle converges superlinearly. f = exit angle - t;
+                 * wa, wb are the Illinois-weighted values used only for the next angle. */
+                double ga = be + M_PI / 2 + M_PI * found / N, gb = be + M_PI / 2 + M_PI * (found + 1) / N;
+                double fa = wrap2pi(ex[(found - 1) * 4] - be) - t, fb = wrap2pi(ex[found * 4] - be) - t;
+                double Ta = ex[(found - 1) * 4 + 1], Tb = ex[found * 4 + 1];
+                double aa = ex[(found - 1) * 4 + 2], ab = ex[found * 4 + 2];
+                int Ka = (int)ex[(found - 1) * 4 + 3], Kb = (int)ex[found * 4 + 3];
+                double wa = fa, wb = fb;
+                int it = 0, side = 0;
+                while (fabs(fa) > tol_rad && fabs(fb) > tol_rad && it < maxit && wb != wa) {
+                    double gc = (ga * wb - gb * wa) / (wb - wa);
+                    int M = og_trace_ray(med, g->R, g->ds, xe, ye, gc, maxs, buf);
                     if (M < 0) break;
                     const osample *L = &buf[M];
-                    double f2 = wrap2pi(atan2(L->y, L->x) - be) - t;
-                    if (f2 > M_PI) f2 -= 2 * M_PI;
-                    if (f2 < -M_PI) f2 += 2 * M_PI;
-                    g0 = g1; f0 = f1; T0 = T1; a0 = a1; K0 = K1;
-                    g1 = g2; f1 = f2; T1 = L->T; a1 = L->a; K1 = L->K;
+                    double fc = wrap2pi(atan2(L->y, L->x) - be) - t;
+                    if (fc > M_PI) fc -= 2 * M_PI;
+                    if (fc < -M_PI) fc += 2 * M_PI;
                     it++;
+                    if ((fc > 0) == (fb > 0)) {          /* c replaces b */
+                        gb = gc; fb = fc; wb = fc; Tb = L->T; ab = L->a; Kb = L->K;
+                        if (side == -1) wa /= 2;
+                        side = -1;
+                    } else {                              /* c replaces a */
+                        ga = gc; fa = fc; wa = fc; Ta = L->T; aa = L->a; Ka = L->K;
+                        if (side == 1) wb /= 2;
+                        side = 1;
+                    }
                 }
-                if (fabs(f1) > tol_rad && fabs(f0) > tol_rad) unconv++;
-                double fr = (f1 == f0) ? 0.0 : (0.0 - f0) / (f1 - f0);   /* exit angle interpolated to t */
-                T = T0 + fr * (T1 - T0);
-                a = a0 + fr * (a1 - a0);
-                K = fabs(f0) <= fabs(f1) ? K0 : K1;
+                if (fabs(fa) > tol_rad && fabs(fb) > tol_rad) unconv++;
+                double fr = (fb == fa) ? 0.0 : (0.0 - fa) / (fb - fa);   /* exit angle interpolated to t */
+                T = Ta + fr * (Tb - Ta);
+                a = aa + fr * (ab - aa);
+                K = fabs(fa) <= fabs(fb) ? Ka : Kb;
             }
             double ph = w * T - M_PI * K / 2 + M_PI / 4;
             o[0] = C * a * cos(ph);

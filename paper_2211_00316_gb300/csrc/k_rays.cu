@@ -679,6 +679,227 @@ void launch_direct_green(const float4 *exits, int N, double f, double c0, float2
     k_direct_green<<<N, 256, smem, s>>>(exits, N, fhi, flo, C, g, counters);
 }
 
+// ---------------------------------------------------------------- ray linking
+
+// One ray from (x, y) to the ring by one thread: the Heun and paraxial step of k_trace_raster
+// (same normalisations, compensated sums and final partial step) without its rasterisation
+// and straight-line shortcuts. The initial direction is formed in double so that a secant
+// iteration on it is not limited by FP32 rounding of the angle. Returns false when the ray
+// does not reach the ring within p.maxs steps.
+template <bool LOSSY, bool RAW>
+__device__ bool trace_one(const float *__restrict__ F, const RayParams &p, float x, float y, double gam0,
+                          float &theta, float &Tout, float &aout, int &Kout)
+{
+    const float ds = p.ds, hds = 0.5f * p.ds, R2 = p.R * p.R;
+    Fv F1;
+    field_eval<LOSSY, RAW>(F, p, x, y, F1);
+    double sd, cd;
+    sincos(gam0, &sd, &cd);
+    float px = F1.n * (float)cd, py = F1.n * (float)sd, dpx = -F1.n * (float)sd, dpy = F1.n * (float)cd;
+    float dxx = 0.f, dxy = 0.f, T = 0.f, Tc = 0.f, B = 0.f, Bc = 0.f;
+    float cx = 0.f, cy = 0.f, cpx = 0.f, cpy = 0.f, cdx = 0.f, cdy = 0.f;
+    float sc1 = 0.f, Jlast = 0.f;
+    int K = 0;
+    for (int i = 0; i < p.maxs; i++) {
+        const float n = F1.n, in = rcp_nr(n);
+        const float sc = n * rsqrtf(px * px + py * py);
+        px *= sc; py *= sc;
+        cpx *= sc; cpy *= sc;
+        const float qx = px * in, qy = py * in;
+        Fv F2;
+        field_eval<LOSSY, RAW>(F, p, x + ds * qx, y + ds * qy, F2);
+        const float na = F2.n, ina = rcp_nr(na);
+        float pax = px + ds * F1.gx, pay = py + ds * F1.gy;
+        const float sca = na * rsqrtf(pax * pax + pay * pay);
+        pax *= sca; pay *= sca;
+        const float qax = pax * ina, qay = pay * ina;
+        const float sx = qx + qax, sy = qy + qay, rs = rsqrtf(sx * sx + sy * sy);
+        const float dirx = sx * rs, diry = sy * rs;
+        const float ddpx = hds * (F1.gx + F2.gx), ddpy = hds * (F1.gy + F2.gy);
+        const float gd = F1.gx * dxx + F1.gy * dxy, pd = px * dpx + py * dpy;
+        const float qdxx = in * (dpx - px * gd * in), qdxy = in * (dpy - py * gd * in);
+        const float w1 = in * (pd * in - gd);
+        const float qdpx = F1.hxx * dxx + F1.hxy * dxy + F1.gx * w1;
+        const float qdpy = F1.hxy * dxx + F1.hyy * dxy + F1.gy * w1;
+        const float dpax = dpx + ds * qdpx, dpay = dpy + ds * qdpy;
+        const float dxax = dxx + ds * qdxx, dxay = dxy + ds * qdxy;
+        const float gda = F2.gx * dxax + F2.gy * dxay, pda = pax * dpax + pay * dpay;
+        const float qdxax = ina * (dpax - pax * gda * ina), qdxay = ina * (dpay - pay * gda * ina);
+        const float w2 = ina * (pda * ina - gda);
+        const float qdpax = F2.hxx * dxax + F2.hxy * dxay + F2.gx * w2;
+        const float qdpay = F2.hxy * dxax + F2.hyy * dxay + F2.gy * w2;
+        const float ddxx = hds * (qdxx + qdxax), ddxy = hds * (qdxy + qdxay);
+        const float ddpx2 = hds * (qdpx + qdpax), ddpy2 = hds * (qdpy + qdpay);
+        const float xn = x + ds * dirx, yn = y + ds * diry;
+        field_eval<LOSSY, RAW>(F, p, xn, yn, F2);
+        float inc = hds * (F1.nr + F2.nr), incB = LOSSY ? hds * (F1.al + F2.al) : 0.f;
+        const bool last = xn * xn + yn * yn >= R2;
+        if (last) {
+            float b = x * dirx + y * diry, cc = x * x + y * y - R2;
+            float disc = b * b - cc;
+            float t = -b + sqrtf(disc > 0.f ? disc : 0.f);
+            t = fminf(fmaxf(t, 0.f), ds);
+            float fr = t / ds;
+            x = x + t * dirx; y = y + t * diry;
+            inc *= fr;
+            incB *= fr;
+            dxx += fr * ddxx; dxy += fr * ddxy;
+            dpx += fr * ddpx2; dpy += fr * ddpy2;
+            px += fr * ddpx; py += fr * ddpy;
+            field_eval<LOSSY, RAW>(F, p, x, y, F2);
+        } else {
+            kadd(x, cx, ds * dirx); kadd(y, cy, ds * diry);
+            kadd(px, cpx, ddpx); kadd(py, cpy, ddpy);
+            kadd(dxx, cdx, ddxx); kadd(dxy, cdy, ddxy);
+            dpx += ddpx2; dpy += ddpy2;
+        }
+        kadd(T, Tc, inc);
+        if (LOSSY) kadd(B, Bc, incB);
+        F1 = F2;
+        const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
+        const float J = dxx * ty - dxy * tx;
+        if (i == 0) { sc1 = sqrtf(F1.nr * fabsf(J) / ds); Jlast = J; }
+        else if (J * Jlast < 0.f) K++;
+        if (J != 0.f) Jlast = J;
+        if (last) {
+            theta = atan2f(y, x);
+            Tout = T;
+            aout = sc1 * rsqrtf(F1.nr * fabsf(J)) * (LOSSY ? expf(-B) : 1.f);
+            Kout = K;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Linked rays of the direct term (Sec. 4.4, Sec. 6.3.2): for each receiver r != e the
+// bracketing fan rays of k_direct_green start a secant iteration on the initial angle, kept
+// inside the bracket (regula falsi with the Illinois weighting), which stops when the exit lies
+// within tol radians of beta_r (at most maxit new rays); T and a are then interpolated in exit
+// angle between the two bracketing rays to beta_r exactly, K taken from the nearer; linked[e][r]
+// = (0, T, a, K) serves every frequency of the trace. Unbracketed receivers take the nearest
+// fan ray; those and the pairs that stopped on maxit are counted in counters[1].
+template <bool LOSSY, bool RAW>
+__global__ void k_link_rays(const float *__restrict__ F, RayParams p, const float4 *__restrict__ exits, int maxit,
+                            double tol, float4 *__restrict__ linked, unsigned long long *counters)
+{
+    extern __shared__ float4 ex[];
+    const int N = p.N;
+    float *th = reinterpret_cast<float *>(ex + (N - 1));
+    const int e = blockIdx.x;
+    const double PI = 3.14159265358979323846, TWO_PI = 2.0 * PI;
+    const double be = TWO_PI * e / N;
+    for (int q = threadIdx.x; q < N - 1; q += blockDim.x) {
+        float4 v = exits[(size_t)e * (N - 1) + q];
+        ex[q] = v;
+        double d = (double)v.x - be;
+        th[q] = (float)(d - TWO_PI * floor(d / TWO_PI));
+    }
+    __syncthreads();
+    const float xe = (float)(p.R * cos(be)), ye = (float)(p.R * sin(be));
+    auto rel = [&](double ang) {
+        double d = ang - be;
+        return d - TWO_PI * floor(d / TWO_PI);
+    };
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+        if (r == e) { linked[(size_t)e * N + r] = make_float4(0.f, 0.f, 0.f, 0.f); continue; }
+        double td = TWO_PI * r / N - be;
+        td -= TWO_PI * floor(td / TWO_PI);
+        const float t = (float)td;
+        int found = -1;
+        for (int j = 1; j <= N - 2; j++) {
+            float tj = th[j - 1], tk = th[j];
+            if (tj == tk) continue;
+            if ((tj <= t && t <= tk) || (tk <= t && t <= tj)) { found = j; break; }
+        }
+        double T, a;
+        int K;
+        if (found > 0) {
+            const float4 A = ex[found - 1], Bq = ex[found];
+            // bracketing secant (regula falsi, Illinois weighting): every new ray starts between
+            // the two bracketing rays, so it points inward like the fan's
+            double ga = be + PI / 2 + PI * found / N, gb = be + PI / 2 + PI * (found + 1) / N;
+            double fa = rel(A.x) - td, fb = rel(Bq.x) - td, wa = fa, wb = fb;
+            double Ta = A.y, Tb = Bq.y, aa = A.z, ab = Bq.z;
+            int Ka = (int)A.w, Kb = (int)Bq.w, it = 0, side = 0;
+            while (fabs(fa) > tol && fabs(fb) > tol && it < maxit && wb != wa) {
+                const double gc = (ga * wb - gb * wa) / (wb - wa);
+                float thc, Tc, ac;
+                int Kc;
+                if (!trace_one<LOSSY, RAW>(F, p, xe, ye, gc, thc, Tc, ac, Kc)) break;
+                double fc = rel(thc) - td;
+                if (fc > PI) fc -= TWO_PI;
+                if (fc < -PI) fc += TWO_PI;
+                it++;
+                if ((fc > 0) == (fb > 0)) {
+                    gb = gc; fb = fc; wb = fc; Tb = Tc; ab = ac; Kb = Kc;
+                    if (side == -1) wa *= 0.5;
+                    side = -1;
+                } else {
+                    ga = gc; fa = fc; wa = fc; Ta = Tc; aa = ac; Ka = Kc;
+                    if (side == 1) wb *= 0.5;
+                    side = 1;
+                }
+            }
+            if (fabs(fa) > tol && fabs(fb) > tol) atomicAdd(&counters[1], 1ull);
+            const double fr = (fb == fa) ? 0.0 : -fa / (fb - fa);
+            T = Ta + fr * (Tb - Ta);
+            a = aa + fr * (ab - aa);
+            K = fabs(fa) <= fabs(fb) ? Ka : Kb;
+        } else {
+            int best = 1;
+            float bd = 1e30f;
+            for (int j = 1; j <= N - 1; j++) {
+                float d = fabsf(th[j - 1] - t);
+                if (d < bd) { bd = d; best = j; }
+            }
+            const float4 A = ex[best - 1];
+            T = A.y; a = A.z; K = (int)A.w;
+            atomicAdd(&counters[1], 1ull);
+        }
+        linked[(size_t)e * N + r] = make_float4(0.f, (float)T, (float)a, (float)K);
+    }
+}
+
+// g[e][r] = C a exp(i 2 pi (f T - K/4 + 1/8)) from the linked rays' (-, T, a, K); 0 on the diagonal
+__global__ void k_green_linked(const float4 *__restrict__ linked, int N, float fhi, float flo, float C,
+                               float2 *__restrict__ g)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)N * N) return;
+    const float4 v = linked[i];
+    if (i / N == i % N) { g[i] = make_float2(0.f, 0.f); return; }
+    float sn, cs;
+    sincospif(2.f * phase_cycles(v.y, (int)v.w, fhi, flo), &sn, &cs);
+    g[i] = make_float2(C * v.z * cs, C * v.z * sn);
+}
+
+void launch_green_linked(const float4 *linked, int N, double f, double c0, float2 *g, cudaStream_t s)
+{
+    float fhi = (float)f, flo = (float)(f - (double)fhi);
+    float C = (float)(1.0 / sqrt(8.0 * 3.14159265358979323846 * (2.0 * 3.14159265358979323846 * f) / c0));
+    const size_t n = (size_t)N * N;
+    k_green_linked<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(linked, N, fhi, flo, C, g);
+}
+
+void launch_link_rays(const float *fields, const RayParams &p, const float4 *exits, int maxit, float4 *linked,
+                      unsigned long long *counters, bool lossy, bool raw, cudaStream_t s)
+{
+    size_t smem = (size_t)(p.N - 1) * (sizeof(float4) + sizeof(float));
+    const double tol = 1e-6;
+#define RBX_LINK(L, W)                                                                                   \
+    do {                                                                                                 \
+        if (smem > 48 * 1024)                                                                            \
+            cudaFuncSetAttribute(k_link_rays<L, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_link_rays<L, W><<<p.N, 128, smem, s>>>(fields, p, exits, maxit, tol, linked, counters);          \
+    } while (0)
+    if (lossy && raw) RBX_LINK(true, true);
+    else if (lossy) RBX_LINK(true, false);
+    else if (raw) RBX_LINK(false, true);
+    else RBX_LINK(false, false);
+#undef RBX_LINK
+}
+
 // ---------------------------------------------------------------- table I/O
 
 __global__ void k_set_tables(const float *T, const float *a, const float *gam, const uint8_t *K, TabEntry *tab,

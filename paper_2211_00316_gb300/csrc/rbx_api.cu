@@ -27,6 +27,8 @@ struct rbx_job {
     double ns_freq = 0.0;      // frequency the fields were made for (lossy fields depend on it)
     bool lossy = false;        // absorption map set (rbx_set_absorption)
     bool raw = false;          // integration on the non-smoothed map (rbx_set_integration)
+    int link_iters = 0;        // secant ray linking of the direct term, new rays per pair (0: off)
+    bool linked_valid = false; // w.linked holds the linked rays of the current tables
     double abs_y = 0.0;
     Workspace w;
     int *d_count = nullptr;
@@ -88,7 +90,7 @@ static void free_ws(Workspace &w, cudaStream_t s)
 {
     void *ps[] = {w.hist, w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
                   w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters, w.alpha0, w.as64,
-                  w.dmacc};
+                  w.dmacc, w.linked};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, s);
     tc_free(w.tc, s);
@@ -187,6 +189,7 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     free_ws(j->w, j->stream);
     keep_pool_memory();
     j->has_geom = j->has_tables = j->ns_valid = j->lossy = j->raw = false;
+    j->link_iters = 0;
     Workspace &w = j->w;
     w.N = g.n_xducers;
     w.nx = g.nx;
@@ -357,6 +360,39 @@ static rbx_status smooth(rbx_job *j, double f)
 
 static bool bad_freq(double f) { return !(std::isfinite(f) && f > 0); }
 
+static RayParams ray_params(const rbx_job *j)
+{
+    const Workspace &w = j->w;
+    RayParams p;
+    p.N = w.N; p.X = w.X; p.nx = w.nx; p.ny = w.ny;
+    p.dx = (float)j->g.dx; p.x0 = (float)j->g.x0; p.y0 = (float)j->g.y0;
+    p.R = (float)j->g.ring_radius; p.ds = (float)j->g.ds; p.inv_dx = (float)(1.0 / j->g.dx);
+    p.rmask = (float)j->g.mask_radius;
+    p.maxs = max_steps(j->g);
+    return p;
+}
+
+// Direct Green's function at the receivers: the fan's exit-angle interpolation, or secant
+// linking of each pair on the current fields (rbx_set_linking), done once per trace and
+// reused by every frequency.
+static rbx_status direct_green(rbx_job *j, double f, float2 *out)
+{
+    Workspace &w = j->w;
+    if (j->link_iters > 0) {
+        if (!j->linked_valid) {
+            launch_link_rays(w.fields, ray_params(j), w.exits, j->link_iters, w.linked, w.counters, j->lossy, j->raw,
+                             j->stream);
+            LAUNCHED(j, 1);
+            j->linked_valid = true;
+        }
+        launch_green_linked(w.linked, w.N, f, j->g.c0, out, j->stream);
+    } else {
+        launch_direct_green(w.exits, w.N, f, j->g.c0, out, w.counters, j->stream);
+    }
+    LAUNCHED(j, 1);
+    return RBX_OK;
+}
+
 rbx_status rbx_trace_rays(rbx_job *j, double f)
 {
     if (!j) return RBX_EINVAL;
@@ -370,15 +406,11 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     if ((st = record(j, EV_FIELDS))) return st;
     CUDA_TRY(j, cudaMemsetAsync(w.tab, 0xff, sizeof(TabEntry) * (size_t)w.N * w.X, j->stream));
     CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
-    RayParams p;
-    p.N = w.N; p.X = w.X; p.nx = w.nx; p.ny = w.ny;
-    p.dx = (float)j->g.dx; p.x0 = (float)j->g.x0; p.y0 = (float)j->g.y0;
-    p.R = (float)j->g.ring_radius; p.ds = (float)j->g.ds; p.inv_dx = (float)(1.0 / j->g.dx);
-    p.rmask = (float)j->g.mask_radius;
-    p.maxs = max_steps(j->g);
+    const RayParams p = ray_params(j);
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
     launch_uniform_radius(w.fields, p, w.counters + 7, j->stream);
     launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->lossy, j->raw, j->stream);
+    j->linked_valid = false;
     LAUNCHED(j, 2);
     if ((st = record(j, EV_TRACE))) return st;
     launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
@@ -396,6 +428,7 @@ rbx_status rbx_set_tables(rbx_job *j, const float *T, const float *a, const floa
     Workspace &w = j->w;
     size_t n = (size_t)w.N * w.X;
     launch_set_tables(T, a, gam, K, w.tab, n, j->stream);
+    j->linked_valid = false;
     CUDA_TRY(j, cudaMemcpyAsync(w.exits, exits, sizeof(float4) * (size_t)w.N * (w.N - 1), cudaMemcpyDeviceToDevice,
                                 j->stream));
     CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
@@ -427,9 +460,11 @@ rbx_status rbx_direct_green(rbx_job *j, double f, void *g_dev)
     if (!j || !g_dev) return RBX_EINVAL;
     NEED(j, j->has_tables, RBX_ESTATE, "rbx_direct_green before rbx_trace_rays or rbx_set_tables");
     NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
-    launch_direct_green(j->w.exits, j->w.N, f, j->g.c0, static_cast<float2 *>(g_dev), j->w.counters, j->stream);
-    LAUNCHED(j, 1);
-    return RBX_OK;
+    if (j->link_iters > 0) {
+        rbx_status st = smooth(j, f);   // the linked rays follow the smoothed map of f
+        if (st) return st;
+    }
+    return direct_green(j, f, static_cast<float2 *>(g_dev));
 }
 
 // D = sum_x G_r G_e v on the current tables, into w.D (symmetric).
@@ -478,8 +513,7 @@ rbx_status rbx_predict(rbx_job *j, double f, void *g_dev)
     Workspace &w = j->w;
     rbx_status st;
     if ((st = smooth(j, f))) return st;
-    launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
-    LAUNCHED(j, 1);
+    if ((st = direct_green(j, f, w.gdir))) return st;
     if (j->raw) {
         // integration on the non-smoothed map: the ray Green's function alone (Sec. 6.3.2)
         CUDA_TRY(j, cudaMemsetAsync(w.D, 0, sizeof(float2) * (size_t)w.N * w.N, j->stream));
@@ -533,8 +567,7 @@ static rbx_status enqueue_freq(rbx_job *j, double f, double df, const float2 *da
 {
     Workspace &w = j->w;
     rbx_status st;
-    launch_direct_green(w.exits, w.N, f, j->g.c0, w.gdir, w.counters, j->stream);
-    LAUNCHED(j, 1);
+    if ((st = direct_green(j, f, w.gdir))) return st;
     if ((st = record(j, EV_GDIR))) return st;
     if (j->raw) {
         // integration on the non-smoothed map: the residual is the ray Green's function alone
@@ -684,6 +717,22 @@ rbx_status rbx_update_frequency(rbx_job *j, double f, double df, const void *dat
     st = update_core(j, f, df, static_cast<const float2 *>(data_dev), out, true);
     if (out) out->n_launches = j->launches - l0;
     return st;
+}
+
+rbx_status rbx_set_linking(rbx_job *j, int max_rays)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_set_linking before rbx_set_geometry");
+    NEED(j, max_rays >= 0 && max_rays <= 32, RBX_EINVAL, "linking takes 0 (off) to 32 new rays per pair");
+    if (max_rays > 0 && !j->w.linked) {
+        if (dalloc(j->w.linked, (size_t)j->w.N * j->w.N, j->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(j, RBX_ENOMEM, "device allocation of the linked rays failed");
+        }
+    }
+    j->link_iters = max_rays;
+    j->linked_valid = false;
+    return RBX_OK;
 }
 
 rbx_status rbx_set_integration(rbx_job *j, int mode)

@@ -64,6 +64,7 @@ struct Workspace {
     float *alpha0 = nullptr;    // absorption map alpha0 [ny][nx], Np (rad/s)^-y m^-1 (lossy jobs only)
     double *as64 = nullptr;     // smoothed alpha0 (lossy jobs only)
     double *dmacc = nullptr;    // sum of a frequency set's search directions per mask node
+    float4 *linked = nullptr;   // linked rays of the direct term [N][N] (0, T, a, K)
     float2 *gdir = nullptr, *D = nullptr, *R = nullptr, *Rs = nullptr, *part = nullptr, *gpart = nullptr;
     float2 *data = nullptr;
     double *red = nullptr;           // reduction scratch
@@ -95,6 +96,11 @@ void launch_uniform_radius(const float *fields, const RayParams &p, unsigned lon
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
                          unsigned long long *counters, bool lossy, bool raw, cudaStream_t s);
 void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s);
+// secant-linked rays of the direct term, linked[e][r] = (0, T, a, K) (maxit new rays per pair at
+// most), and the direct Green's function of one frequency from them
+void launch_link_rays(const float *fields, const RayParams &p, const float4 *exits, int maxit, float4 *linked,
+                      unsigned long long *counters, bool lossy, bool raw, cudaStream_t s);
+void launch_green_linked(const float4 *linked, int N, double f, double c0, float2 *g, cudaStream_t s);
 void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, unsigned long long *counters, cudaStream_t s);
 void launch_direct_green(const float4 *exits, int N, double f, double c0, float2 *g, unsigned long long *counters,
                          cudaStream_t s);

@@ -83,6 +83,7 @@ _SIGS = {
     "rbx_server_cancel": [_P, C.c_longlong],
     "rbx_set_absorption": [_P, _P, C.c_double],
     "rbx_set_integration": [_P, C.c_int],
+    "rbx_set_linking": [_P, C.c_int],
     "rbx_update_set": [_P, C.POINTER(C.c_double), C.c_int, C.c_double, _P, C.POINTER(Stats)],
     "rbx_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
@@ -218,6 +219,10 @@ class Job:
     def set_integration(self, raw: bool):
         """True: integrate on the non-smoothed map, no Born term (rbx_set_integration mode 1)."""
         self._check(self.L.rbx_set_integration(self.h, 1 if raw else 0))
+
+    def set_linking(self, max_rays: int):
+        """Secant linking of the direct term with at most max_rays new rays per pair (0: off)."""
+        self._check(self.L.rbx_set_linking(self.h, int(max_rays)))
 
     def update_set(self, freqs, df: float, data: torch.Tensor) -> dict:
         """One update from a frequency set; data [nf][N][N] complex64 on the device."""

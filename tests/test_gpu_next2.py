@@ -116,3 +116,61 @@ def test_set_argument_errors(work):
         j.update_set([3e5, float("nan")], 1e5, data)
     assert j.L.rbx_set_integration(j.h, 2) == 1          # RBX_EINVAL
     j.close()
+
+
+def test_linked_direct_green_water(oracle_mod):
+    """In water the linked rays are the chords: g = App. B's g0 (and the fan already links)."""
+    w = P.custom(64, 96, 1e-3, 45e-3, kind="water", freqs=(3e5,))
+    j = rbx.Job()
+    j.set_geometry(w.geom)
+    j.set_model(dev(np.full((96, 96), 1500.0, np.float32)))
+    j.set_linking(6)
+    j.trace_rays(3e5)
+    g = j.direct_green(3e5).cpu().numpy()
+    N = 64
+    k = 2 * math.pi * 3e5 / 1500.0
+    b = 2 * math.pi * np.arange(N) / N
+    xy = 45e-3 * np.stack([np.cos(b), np.sin(b)], 1)
+    s = np.linalg.norm(xy[:, None, :] - xy[None, :, :], axis=-1)
+    off = ~np.eye(N, dtype=bool)
+    ref = (8 * math.pi * k * s[off]) ** -0.5 * np.exp(1j * (k * s[off] + math.pi / 4))
+    assert rel_l2(g[off], ref) <= 1e-4          # own FP32 rays (T to ~1e-11 s, grazing a floor)
+    j.close()
+
+
+@pytest.mark.parametrize("raw", [False, True])
+def test_linked_direct_green_parity(work, oracle_mod, raw):
+    """Secant-linked direct Green's function against the oracle's, on each side's own rays."""
+    o = oracle_mod.Oracle(work.geom)
+    f = float(work.freqs[0])
+    c_t = work.c_true.astype(np.float32).astype(np.float64)
+    j = job_for(work, raw=raw)
+    j.set_linking(8)
+    j.set_model(dev(c_t.astype(np.float32)))
+    j.trace_rays(f)
+    g_gpu = j.direct_green(f).cpu().numpy()
+    ns, f6 = o.fields_for(c_t, f)
+    tb = o.tables(f6, nr=(1.0 / c_t) if raw else None)
+    g_orc, cl, unc, Tl = o.direct_green_linked(f, f6, tb.exits, nr=(1.0 / c_t) if raw else None)
+    assert unc == 0
+    assert rel_l2(g_gpu, g_orc) <= 1e-4
+    j.close()
+
+
+def test_linked_set_update(work, oracle_mod):
+    """One two-frequency update with linked rays and the non-smoothed integration (the paper's
+    configuration) on each side: <= 0.05 m/s RMS."""
+    o = oracle_mod.Oracle(work.geom)
+    freqs = [float(work.freqs[0]), float(work.freqs[0]) + 5e4]
+    c_t = work.c_true.astype(np.float32).astype(np.float64)
+    c64 = work.c_init.astype(np.float32).astype(np.float64)
+    data = np.stack([o.predict_ext(f, c_t, raw=True, link=True)[0] for f in freqs])
+    c_ref, st_ref, bad = o.update_set(freqs, 5e4, c64, data, raw=True, link=True)
+    assert bad == 0
+    j = job_for(work, rbx.RBX_BF16, raw=True)
+    j.set_linking(8)
+    j.update_set(freqs, 5e4, dev(data, torch.complex64))
+    c_gpu = j.get_model().cpu().numpy().astype(np.float64)
+    m = work.geom.mask()
+    assert np.sqrt(np.mean((c_gpu[m] - c_ref[m]) ** 2)) <= 0.05
+    j.close()
