@@ -6,6 +6,7 @@ they compare with closed forms (App. B, linear-velocity rays), library routines
 condition, adjoint identity, symmetry) and values the paper prints (window sizes).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -34,14 +35,38 @@ def g0(f, s, c0=C0):
 # --------------------------------------------------------------- a1
 
 
+def golden(name):
+    """key = values from tests/golden/<name> (comments after #)."""
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = (t.strip() for t in line.split("=", 1))
+                out[k] = [float(x) for x in v.split()]
+    return out
+
+
 def test_window_values_printed_in_paper(oracle_mod):
-    """Sec. 6.2: window 7 at 1 MHz on a 1 mm grid, and 17 on the 0.4 mm grid."""
+    """Sec. 6.2: window 7 at 1 MHz on a 1 mm grid, and 17 on the 0.4 mm grid; Sec. 6.3.2:
+    13, 11, 9, 7 from low to high frequency on a 1 mm grid (tests/golden)."""
+    gv = golden("paper_printed_values.txt")
     o1 = oracle_mod.Oracle(ring_geom(dx=1e-3))
     o2 = oracle_mod.Oracle(ring_geom(dx=0.4e-3, nx=240))
-    assert o1.window(1.0e6) == 7
-    assert o2.window(1.0e6) == 17
-    # 13, 11, 9, 7 decreasing from low to high frequency on a 1 mm grid (Sec. 6.3.2)
-    assert [o1.window(f) for f in (0.2e6, 0.5e6, 0.8e6, 1.2e6)] == [13, 11, 9, 7]
+    assert o1.window(1.0e6) == gv["window_1mm_1MHz"][0]
+    assert o2.window(1.0e6) == gv["window_0.4mm_1MHz"][0]
+    assert [o1.window(f) for f in (0.2e6, 0.5e6, 0.8e6, 1.2e6)] == gv["windows_1mm_low_to_high"]
+
+
+def test_step_length_reading_matches_printed_sweep():
+    """Reading 12: tau per update scales with the frequency band per update; for the paper's own
+    sweep (Sec. 6.3.2a) the printed tau is recovered, and one frequency per update at twice the
+    band takes the same tau."""
+    gv = golden("paper_printed_values.txt")
+    nf, f0, f1 = gv["sweep_frequencies"][0], gv["sweep_fmin_MHz"][0], gv["sweep_fmax_MHz"][0]
+    df = (f1 - f0) * 1e6 / (nf - 1)
+    per = gv["frequencies_per_update"][0]
+    assert P.step_length(per * df) == pytest.approx(gv["step_length"][0], rel=1e-12)
 
 
 def test_smoothing_is_uniform_filter(oracle_mod):
