@@ -94,7 +94,7 @@ def kernel_src_hash(kernel: str) -> str:
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:k_trace_raster
     #     -s 2 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --serve-requests 0 (1 pass)
-    ("precision_ring1024", "trace"): {"bytes": 2.518852864e9 + 2.458076160e9, "src": "4405b6ae7d56"},
+    ("precision_ring1024", "trace"): {"bytes": 2.518314240e9 + 2.457521152e9, "src": "24a6b04a0055"},
 }
 
 
@@ -110,9 +110,14 @@ def algorithmic(kernel: str, N: int, X: int, precision: str):
     if kernel == "synth_fwd":
         return (16.0 + 8.0) * NX, "byte", "hbm"
     if kernel == "synth_bp":
-        return (16.0 + 4.0 + 16.0) * NX, "byte", "hbm"
+        # tables in; FP32: angular density in, U and kappa out; BF16: 6 planes out (x2 when split)
+        out = {"fp32": 4.0 + 16.0, "bf16": 12.0, "bf16x3": 24.0}[precision]
+        return (16.0 + out) * NX, "byte", "hbm"
     if kernel == "tables":
-        return (16.0 * 3 + 4.0) * NX, "byte", "hbm"
+        # direct Green's function (exits in, N x N complex out); FP32 also forms the angular
+        # density array (tables in, one float out per entry)
+        green = 16.0 * N * (N - 1) + 8.0 * N * N
+        return green + ((16.0 + 4.0) * NX if precision == "fp32" else 0.0), "byte", "hbm"
     return None, None, None
 
 

@@ -398,42 +398,74 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *_
 }
 
 // planes [6][Xp][Npad] at [x][e]: u, conj(kappa) u, kappa u (re, im each);
-// u_e[x] = dgamma / (C a) exp(-i 2 pi (f T - K/4 + 1/8)), kappa = exp(i gamma)
-__global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, const float *__restrict__ dg, int N, int X, int Npad,
-                              size_t pstride, float fhi, float flo, float C, __nv_bfloat16 *__restrict__ planes,
-                              int split)
+// u_e[x] = dgamma / (C a) exp(-i 2 pi (f T - K/4 + 1/8)), kappa = exp(i gamma).
+// The angular density dgamma (step a4) is formed here from the direction angles of the
+// neighbouring transducers: a 32-transducer tile reads one halo row on each side (rows wrap
+// around the ring), so the tables are read once more by 1/16 instead of a separate pass.
+__global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, int N, int X, int Npad, size_t pstride, float fhi,
+                              float flo, float C, __nv_bfloat16 *__restrict__ planes, int split)
 {
     __shared__ float sv[6][32][33];
+    __shared__ float sg[34][32];            // gamma of rows e0 - 1 .. e0 + 32 (mod N)
+    __shared__ unsigned char sc[34][32];    // covered flags of the same
     const int x0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    for (int q = ty; q < 32; q += 8) {
-        int e = e0 + q, x = x0 + tx;
+    const int x = x0 + tx;
+    TabEntry t[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        // slot q + 1 holds row (e0 + q) mod N: past the last transducer (ragged last tile) it
+        // is the ring's wrap, row 0 being the next neighbour of row N - 1
+        const int q = ty + 8 * k, e = e0 + q;
+        TabEntry r;
+        r.idk = kUncovered;
+        r.T = r.a = r.gam = 0.f;
+        if (x < X) r = tab[(size_t)(e % N) * X + x];
+        sg[q + 1][tx] = r.gam;
+        sc[q + 1][tx] = r.idk != kUncovered;
+        if (e >= N) r.idk = kUncovered;   // not a row of this tile's output
+        t[k] = r;
+    }
+    if (ty < 2) {   // halo rows: slot 0 is row (e0 - 1) mod N, slot 33 row (e0 + 32) mod N
+        const int slot = ty == 0 ? 0 : 33;
+        const int e = (int)(((long long)e0 - 1 + slot + N) % N);
+        TabEntry h;
+        h.idk = kUncovered;
+        h.gam = 0.f;
+        if (x < X) h = tab[(size_t)e * X + x];
+        sg[slot][tx] = h.gam;
+        sc[slot][tx] = h.idk != kUncovered;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int q = ty + 8 * k;
         float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (e < N && x < X) {
-            size_t i = (size_t)e * X + x;
-            TabEntry t = tab[i];
-            if (t.idk != kUncovered) {
-                float s, c, sg, cg;
-                sincospif(2.f * phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &s, &c);
-                sincosf(t.gam, &sg, &cg);
-                float A = dg[i] / (C * t.a);
-                float ur = A * c, ui = -A * s;
-                v[0] = ur; v[1] = ui;
-                v[2] = cg * ur + sg * ui; v[3] = cg * ui - sg * ur;   // conj(kappa) u
-                v[4] = cg * ur - sg * ui; v[5] = cg * ui + sg * ur;   // kappa u
-            }
+        if (t[k].idk != kUncovered) {
+            // slot q + 2 is row (e + 1) mod N and slot q row (e - 1) mod N, also for e = 0, N - 1
+            const float dg = (sc[q + 2][tx] && sc[q][tx]) ? dgamma_of(sg[q + 2][tx], sg[q][tx]) : 0.f;
+            // kappa from the hardware sine / cosine (gamma lies in [-pi, pi], absolute error
+            // ~1e-6, far below the BF16 planes' and the split planes' 2^-16 resolution)
+            float sn, cs, sgm, cgm;
+            sincospif(2.f * phase_cycles_tc(t[k].T, (int)(t[k].idk & 0xffu), fhi, flo), &sn, &cs);
+            __sincosf(t[k].gam, &sgm, &cgm);
+            const float A = dg * rcp_nr(C * t[k].a);
+            float ur = A * cs, ui = -A * sn;
+            v[0] = ur; v[1] = ui;
+            v[2] = cgm * ur + sgm * ui; v[3] = cgm * ui - sgm * ur;   // conj(kappa) u
+            v[4] = cgm * ur - sgm * ui; v[5] = cgm * ui + sgm * ur;   // kappa u
         }
 #pragma unroll
-        for (int k = 0; k < 6; k++) sv[k][q][tx] = v[k];
+        for (int m = 0; m < 6; m++) sv[m][q][tx] = v[m];
     }
     __syncthreads();
     for (int q = ty; q < 32; q += 8) {
-        int x = x0 + q, e = e0 + tx;
-        if (x < X && e < N) {
-            size_t o = (size_t)x * Npad + e;
+        int xo = x0 + q, e = e0 + tx;
+        if (xo < X && e < N) {
+            size_t o = (size_t)xo * Npad + e;
 #pragma unroll
-            for (int k = 0; k < 6; k++)
-                put_split(planes + k * pstride + o, split ? planes + (6 + k) * pstride + o : nullptr, sv[k][tx][q]);
+            for (int m = 0; m < 6; m++)
+                put_split(planes + m * pstride + o, split ? planes + (6 + m) * pstride + o : nullptr, sv[m][tx][q]);
         }
     }
 }
@@ -686,11 +718,11 @@ int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s)
     return p.fwd_splits;
 }
 
-void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, double f, double c0, cudaStream_t s)
+void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, double f, double c0, cudaStream_t s)
 {
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
-    k_synth_bp_tc<<<grd, 256, 0, s>>>(tab, dg, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
+    k_synth_bp_tc<<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
                                       static_cast<__nv_bfloat16 *>(p.bplanes), p.split);
 }
 

@@ -18,6 +18,8 @@
 //
 // Fields are bilinearly interpolated from the 8-float-per-node field map (L1/L2 cached:
 // 8 MB at 512^2). Travel time uses compensated (Kahan) summation.
+#include <climits>
+
 #include "rbx_internal.cuh"
 
 namespace rbx {
@@ -28,16 +30,6 @@ struct Fv {
     float n, gx, gy, hxx, hxy, hyy, al;   // al: absorption coefficient alpha (lossy media only)
     float nr;                              // slowness integrated along the ray (n, or the non-smoothed one)
 };
-
-// 1/v for v in the range of a slowness or a triangle's edge sum: the hardware approximation
-// refined by one Newton-Raphson step, r <- r + r (1 - v r) (no special cases: v is finite
-// and away from 0 and the denormal range here).
-__device__ __forceinline__ float rcp_nr(float v)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-    return fmaf(fmaf(-v, r, 1.f), r, r);
-}
 
 // s += inc with compensation term c (Kahan): the ray state is a sum of ~10^3 small steps
 __device__ __forceinline__ void kadd(float &s, float &c, float inc)
@@ -114,11 +106,13 @@ __device__ __forceinline__ void cas_min_from(TabEntry *e, unsigned long long key
 struct HitQueue {
     int *xi;
     unsigned long long *key;
-    float4 *v;   // (a, kappa_x, kappa_y, -)
-    int n;       // warp-uniform
+    float4 *v;       // (a, kappa_x, kappa_y, -)
+    unsigned *cov;   // entries this warp found untouched (each entry is found so exactly once)
+    int n;           // warp-uniform
 };
 
-__device__ __forceinline__ void drain_one(const HitQueue &hq, int q, TabEntry *fan, unsigned long long *counters)
+// Returns true when this exchange was the entry's first write.
+__device__ __forceinline__ bool drain_one(const HitQueue &hq, int q, TabEntry *fan, unsigned long long *counters)
 {
     const float4 v = hq.v[q];
     const unsigned long long key = hq.key[q];
@@ -127,7 +121,16 @@ __device__ __forceinline__ void drain_one(const HitQueue &hq, int q, TabEntry *f
     // most entries are still untouched (all ones): try that first, then take the minimum
     unsigned long long lo, hi;
     cas128(reinterpret_cast<unsigned long long *>(addr), ~0ull, ~0ull, key, pay, lo, hi);
-    if (!(lo == ~0ull && hi == ~0ull)) cas_min_from(addr, key, pay, lo, hi, counters);
+    if (lo == ~0ull && hi == ~0ull) return true;
+    cas_min_from(addr, key, pay, lo, hi, counters);
+    return false;
+}
+
+// Adds the warp's first writes to its count of covered entries (all lanes take part).
+__device__ __forceinline__ void count_first(const HitQueue &hq, bool first)
+{
+    const unsigned b = __ballot_sync(0xffffffffu, first);
+    if ((threadIdx.x & 31) == 0) *hq.cov += __popc(b);
 }
 
 // Edge function of P -> Q at (px, py), always evaluated from the vertex with the smaller
@@ -271,7 +274,7 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
             hq.n += __popc(b);
             __syncwarp();
             if (hq.n >= 32) {
-                drain_one(hq, hq.n - 32 + lane, fan, counters);
+                count_first(hq, drain_one(hq, hq.n - 32 + lane, fan, counters));
                 hq.n -= 32;
                 __syncwarp();
             }
@@ -289,7 +292,9 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
     __shared__ int q_xi[4][64];
     __shared__ unsigned long long q_key[4][64];
     __shared__ float4 q_v[4][64];
+    __shared__ unsigned q_cov[4];
     for (int q = threadIdx.x; q < p.ny; q += blockDim.x) rows[q] = rows_g[q];
+    if (threadIdx.x < 4) q_cov[threadIdx.x] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -301,7 +306,7 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
     const bool has_ray = j <= N - 1;
     TabEntry *fan = tab + (size_t)e * p.X;
     const float ds = p.ds, hds = 0.5f * p.ds, inv_dx = p.inv_dx, R2 = p.R * p.R;
-    HitQueue hq{q_xi[wib], q_key[wib], q_v[wib], 0};
+    HitQueue hq{q_xi[wib], q_key[wib], q_v[wib], &q_cov[wib], 0};
 
     const double be = 2.0 * 3.14159265358979323846 * e / N;
     float x = (float)(p.R * cos(be)), y = (float)(p.R * sin(be));
@@ -503,8 +508,10 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
         if (!__any_sync(FULL, alive)) break;
         if (i == p.maxs - 1 && alive) atomicAdd(&counters[2], 1ull);   // ray never reached the ring
     }
-    // drain the rest of the queue
-    if (lane < hq.n) drain_one(hq, lane, fan, counters);
+    // drain the rest of the queue; the covered-entry count goes to counters[0]
+    count_first(hq, lane < hq.n && drain_one(hq, lane, fan, counters));
+    __syncwarp();
+    if (lane == 0 && *hq.cov) atomicAdd(&counters[0], (unsigned long long)*hq.cov);
 }
 
 // Largest radius of a node whose fields differ from the uniform medium of node (0, 0)
@@ -573,26 +580,22 @@ void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_
 
 // ---------------------------------------------------------------- a4
 
-__global__ void k_dgamma(const TabEntry *__restrict__ tab, float *__restrict__ dg, int N, int X,
-                         unsigned long long *counters)
+// Angular density of every entry (the back-projection's tensor-core operand synthesis forms
+// the same values itself, from the same expression, and does not need this array).
+__global__ void k_dgamma(const TabEntry *__restrict__ tab, float *__restrict__ dg, int N, int X)
 {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= (size_t)N * X) return;
     int e = (int)(i / X), k = (int)(i % X);
     const TabEntry &tp = tab[(size_t)((e + 1) % N) * X + k];
     const TabEntry &tm = tab[(size_t)((e + N - 1) % N) * X + k];
-    if (tab[i].idk == kUncovered) atomicAdd(&counters[0], 1ull);
-    if (tp.idk == kUncovered || tm.idk == kUncovered) { dg[i] = 0.f; return; }
-    float d = tp.gam - tm.gam;
-    const float PI = 3.14159265358979f, TWO_PI = 6.28318530717959f;
-    d = d - TWO_PI * floorf((d + PI) / TWO_PI);
-    dg[i] = 0.5f * fabsf(d);
+    dg[i] = (tp.idk == kUncovered || tm.idk == kUncovered) ? 0.f : dgamma_of(tp.gam, tm.gam);
 }
 
-void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, unsigned long long *counters, cudaStream_t s)
+void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, cudaStream_t s)
 {
     size_t n = (size_t)N * X;
-    k_dgamma<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, dg, N, X, counters);
+    k_dgamma<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, dg, N, X);
 }
 
 // ---------------------------------------------------------------- a5
@@ -613,42 +616,76 @@ __device__ __forceinline__ float wrap2pi(float t)
     return t - TWO_PI * floorf(t / TWO_PI);
 }
 
+// Angle of receiver r relative to transducer e, in [0, 2 pi): (r - e) mod N ring steps of
+// step = 2 pi / N (no FP64 division or rounding to whole turns: FP64 is slow on this GPU).
+__device__ __forceinline__ double recv_rel(int r, int e, int N, double step)
+{
+    return (double)((r - e + N) % N) * step;
+}
+
+// An angle difference d in (-4 pi, 4 pi) taken to [0, 2 pi) by whole turns.
+__device__ __forceinline__ double wrap_turn(double d)
+{
+    const double TWO_PI = 6.283185307179586476925;
+    if (d < 0.0) d += TWO_PI;
+    if (d < 0.0) d += TWO_PI;
+    if (d >= TWO_PI) d -= TWO_PI;
+    if (d >= TWO_PI) d -= TWO_PI;
+    return d;
+}
+
+// For every receiver r != e of fan e, the first pair of consecutive fan rays (j, j + 1),
+// j = 1..N-2, whose exit angles th (relative to beta_e, in [0, 2 pi)) bracket beta_r, as
+// first[r] = j, or INT_MAX when no pair does. Each pair marks the receivers between its two
+// exit angles (the bracket test on the candidates around them) and the smallest j wins, so a
+// fan costs O(N) rather than a scan over the pairs per receiver. Called by the whole block.
+__device__ void first_brackets(const float *th, int N, int e, double step, int *first)
+{
+    for (int r = threadIdx.x; r < N; r += blockDim.x) first[r] = INT_MAX;
+    __syncthreads();
+    const float scale = (float)N * 0.159154943091895f;   // receivers per radian
+    for (int j = 1 + threadIdx.x; j <= N - 2; j += blockDim.x) {
+        const float tj = th[j - 1], tk = th[j];
+        if (tj == tk) continue;
+        const float lo = fminf(tj, tk), hi = fmaxf(tj, tk);
+        const int m0 = max(1, (int)floorf(lo * scale) - 1), m1 = min(N - 1, (int)ceilf(hi * scale) + 1);
+        for (int m = m0; m <= m1; m++) {
+            const int r = (e + m) % N;
+            const float t = (float)((double)m * step);   // recv_rel(r, e, N, step)
+            if ((tj <= t && t <= tk) || (tk <= t && t <= tj)) atomicMin(&first[r], j);
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void k_direct_green(const float4 *__restrict__ exits, int N, float fhi, float flo, float C,
                                float2 *__restrict__ g, unsigned long long *counters)
 {
     extern __shared__ float4 ex[];
     float *th = reinterpret_cast<float *>(ex + (N - 1));   // exit angle relative to beta_e, in [0, 2 pi)
+    int *first = reinterpret_cast<int *>(th + (N - 1));    // first bracketing pair per receiver
     const int e = blockIdx.x;
-    const double TWO_PI = 6.283185307179586476925;
-    const double be = TWO_PI * e / N;
+    const double step = 6.283185307179586476925 / N, be = (double)e * step;
     for (int q = threadIdx.x; q < N - 1; q += blockDim.x) {
         float4 v = exits[(size_t)e * (N - 1) + q];
         ex[q] = v;
-        double d = (double)v.x - be;
-        th[q] = (float)(d - TWO_PI * floor(d / TWO_PI));
+        th[q] = (float)wrap_turn((double)v.x - be);
     }
     __syncthreads();
+    first_brackets(th, N, e, step, first);
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
         if (r == e) { g[(size_t)e * N + r] = make_float2(0.f, 0.f); continue; }
-        double td = TWO_PI * r / N - be;
-        td -= TWO_PI * floor(td / TWO_PI);
-        float t = (float)td;
+        const double td = recv_rel(r, e, N, step);
+        const float t = (float)td;
         // first consecutive pair (j, j+1) whose exit angles bracket beta_r
-        int found = -1;
-        for (int j = 1; j <= N - 2; j++) {
-            float tj = th[j - 1], tk = th[j];
-            if (tj == tk) continue;
-            if ((tj <= t && t <= tk) || (tk <= t && t <= tj)) { found = j; break; }
-        }
+        const int found = first[r] == INT_MAX ? -1 : first[r];
         float T, a;
         int K;
         if (found > 0) {
             float4 A = ex[found - 1], B = ex[found];
             // the bracket fraction from the exit angles in double precision
-            double ta = (double)A.x - be, tb = (double)B.x - be;
-            ta -= TWO_PI * floor(ta / TWO_PI);
-            tb -= TWO_PI * floor(tb / TWO_PI);
-            double fr = (td - ta) / (tb - ta);
+            const double ta = wrap_turn((double)A.x - be), tb = wrap_turn((double)B.x - be);
+            const double fr = (td - ta) / (tb - ta);
             T = (float)((double)A.y + fr * ((double)B.y - (double)A.y));
             a = (float)((double)A.z + fr * ((double)B.z - (double)A.z));
             K = (int)(fr < 0.5 ? A.w : B.w);
@@ -674,7 +711,7 @@ void launch_direct_green(const float4 *exits, int N, double f, double c0, float2
 {
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     float C = (float)(1.0 / sqrt(8.0 * 3.14159265358979323846 * (2.0 * 3.14159265358979323846 * f) / c0));
-    size_t smem = (size_t)(N - 1) * (sizeof(float4) + sizeof(float));   // <= 82 KB for N <= 4095
+    size_t smem = (size_t)(N - 1) * (sizeof(float4) + sizeof(float)) + (size_t)N * sizeof(int);   // <= 98 KB
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_direct_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_direct_green<<<N, 256, smem, s>>>(exits, N, fhi, flo, C, g, counters);
 }
@@ -786,32 +823,24 @@ __global__ void k_link_rays(const float *__restrict__ F, RayParams p, const floa
     extern __shared__ float4 ex[];
     const int N = p.N;
     float *th = reinterpret_cast<float *>(ex + (N - 1));
+    int *first = reinterpret_cast<int *>(th + (N - 1));
     const int e = blockIdx.x;
     const double PI = 3.14159265358979323846, TWO_PI = 2.0 * PI;
-    const double be = TWO_PI * e / N;
+    const double step = TWO_PI / N, be = (double)e * step;
     for (int q = threadIdx.x; q < N - 1; q += blockDim.x) {
         float4 v = exits[(size_t)e * (N - 1) + q];
         ex[q] = v;
-        double d = (double)v.x - be;
-        th[q] = (float)(d - TWO_PI * floor(d / TWO_PI));
+        th[q] = (float)wrap_turn((double)v.x - be);
     }
     __syncthreads();
+    first_brackets(th, N, e, step, first);
     const float xe = (float)(p.R * cos(be)), ye = (float)(p.R * sin(be));
-    auto rel = [&](double ang) {
-        double d = ang - be;
-        return d - TWO_PI * floor(d / TWO_PI);
-    };
+    auto rel = [&](double ang) { return wrap_turn(ang - be); };
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
         if (r == e) { linked[(size_t)e * N + r] = make_float4(0.f, 0.f, 0.f, 0.f); continue; }
-        double td = TWO_PI * r / N - be;
-        td -= TWO_PI * floor(td / TWO_PI);
+        const double td = recv_rel(r, e, N, step);
         const float t = (float)td;
-        int found = -1;
-        for (int j = 1; j <= N - 2; j++) {
-            float tj = th[j - 1], tk = th[j];
-            if (tj == tk) continue;
-            if ((tj <= t && t <= tk) || (tk <= t && t <= tj)) { found = j; break; }
-        }
+        const int found = first[r] == INT_MAX ? -1 : first[r];
         double T, a;
         int K;
         if (found > 0) {
@@ -885,7 +914,7 @@ void launch_green_linked(const float4 *linked, int N, double f, double c0, float
 void launch_link_rays(const float *fields, const RayParams &p, const float4 *exits, int maxit, float4 *linked,
                       unsigned long long *counters, bool lossy, bool raw, cudaStream_t s)
 {
-    size_t smem = (size_t)(p.N - 1) * (sizeof(float4) + sizeof(float));
+    size_t smem = (size_t)(p.N - 1) * (sizeof(float4) + sizeof(float)) + (size_t)p.N * sizeof(int);
     const double tol = 1e-6;
 #define RBX_LINK(L, W)                                                                                   \
     do {                                                                                                 \
@@ -902,24 +931,30 @@ void launch_link_rays(const float *fields, const RayParams &p, const float4 *exi
 
 // ---------------------------------------------------------------- table I/O
 
+// counters[0] gains the number of covered entries (a > 0).
 __global__ void k_set_tables(const float *T, const float *a, const float *gam, const uint8_t *K, TabEntry *tab,
-                             size_t n)
+                             size_t n, unsigned long long *counters)
 {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    TabEntry t;
-    float av = a[i];
-    t.idk = av > 0.f ? (uint32_t)K[i] : kUncovered;
-    t.T = T[i];
-    t.a = av;
-    t.gam = gam[i];
-    tab[i] = t;
+    bool cov = false;
+    if (i < n) {
+        TabEntry t;
+        float av = a[i];
+        cov = av > 0.f;
+        t.idk = cov ? (uint32_t)K[i] : kUncovered;
+        t.T = T[i];
+        t.a = av;
+        t.gam = gam[i];
+        tab[i] = t;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, cov);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&counters[0], (unsigned long long)__popc(b));
 }
 
 void launch_set_tables(const float *T, const float *a, const float *gam, const uint8_t *K, TabEntry *tab, size_t n,
-                       cudaStream_t s)
+                       unsigned long long *counters, cudaStream_t s)
 {
-    k_set_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(T, a, gam, K, tab, n);
+    k_set_tables<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(T, a, gam, K, tab, n, counters);
 }
 
 __global__ void k_get_tables(const TabEntry *tab, float *T, float *a, float *gam, uint8_t *K, size_t n)

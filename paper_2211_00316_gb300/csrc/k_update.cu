@@ -265,22 +265,23 @@ namespace rbx {
 // slot = (|R|^2, sum dc^2, max |dc|, sum dm^2, uncovered, clamped, bad rays, CAS bound,
 //         non-positive m, bad model, tensor-core timeout, 0)
 __global__ void k_snapshot(const double *r2, const double *upd3, const unsigned long long *counters,
-                           const unsigned *tc_err, double *slot)
+                           const unsigned *tc_err, unsigned long long n_entries, double *slot)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     slot[0] = *r2;
     slot[1] = upd3[0];
     slot[2] = upd3[1];
     slot[3] = upd3[2];
-    for (int k = 0; k < 6; k++) slot[4 + k] = (double)counters[k];
+    slot[4] = (double)(n_entries - counters[0]);   // counters[0] holds the covered entries
+    for (int k = 1; k < 6; k++) slot[4 + k] = (double)counters[k];
     slot[10] = tc_err ? (double)*tc_err : 0.0;
     slot[11] = 0.0;
 }
 
 void launch_snapshot(const double *r2, const double *upd3, const unsigned long long *counters, const unsigned *tc_err,
-                     double *slot, cudaStream_t s)
+                     unsigned long long n_entries, double *slot, cudaStream_t s)
 {
-    k_snapshot<<<1, 32, 0, s>>>(r2, upd3, counters, tc_err, slot);
+    k_snapshot<<<1, 32, 0, s>>>(r2, upd3, counters, tc_err, n_entries, slot);
 }
 
 // dst = (first ? 0 : dst) + src: the residual norm summed over a frequency set

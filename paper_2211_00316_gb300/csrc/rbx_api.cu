@@ -29,6 +29,7 @@ struct rbx_job {
     bool raw = false;          // integration on the non-smoothed map (rbx_set_integration)
     int link_iters = 0;        // secant ray linking of the direct term, new rays per pair (0: off)
     bool linked_valid = false; // w.linked holds the linked rays of the current tables
+    bool dg_valid = false;     // w.dg holds the angular density of the current tables
     double abs_y = 0.0;
     Workspace w;
     int *d_count = nullptr;
@@ -393,6 +394,18 @@ static rbx_status direct_green(rbx_job *j, double f, float2 *out)
     return RBX_OK;
 }
 
+// The angular density array w.dg (step a4), formed when first needed after the tables changed:
+// the FP32 back-projection and rbx_get_tables read it; the tensor-core operand synthesis forms
+// the same values from the tables itself.
+static rbx_status ensure_dgamma(rbx_job *j)
+{
+    if (j->dg_valid) return RBX_OK;
+    launch_dgamma(j->w.tab, j->w.dg, j->w.N, j->w.X, j->stream);
+    LAUNCHED(j, 1);
+    j->dg_valid = true;
+    return RBX_OK;
+}
+
 rbx_status rbx_trace_rays(rbx_job *j, double f)
 {
     if (!j) return RBX_EINVAL;
@@ -410,11 +423,10 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
     launch_uniform_radius(w.fields, p, w.counters + 7, j->stream);
     launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->lossy, j->raw, j->stream);
-    j->linked_valid = false;
+    j->linked_valid = j->dg_valid = false;
     LAUNCHED(j, 2);
     if ((st = record(j, EV_TRACE))) return st;
-    launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
-    LAUNCHED(j, 1);
+    if (j->g.precision == RBX_FP32 && (st = ensure_dgamma(j))) return st;
     if ((st = record(j, EV_TABLES))) return st;
     j->has_tables = true;
     return RBX_OK;
@@ -427,13 +439,12 @@ rbx_status rbx_set_tables(rbx_job *j, const float *T, const float *a, const floa
     NEED(j, j->has_geom, RBX_ESTATE, "rbx_set_tables before rbx_set_geometry");
     Workspace &w = j->w;
     size_t n = (size_t)w.N * w.X;
-    launch_set_tables(T, a, gam, K, w.tab, n, j->stream);
-    j->linked_valid = false;
+    CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
+    launch_set_tables(T, a, gam, K, w.tab, n, w.counters, j->stream);
+    j->linked_valid = j->dg_valid = false;
     CUDA_TRY(j, cudaMemcpyAsync(w.exits, exits, sizeof(float4) * (size_t)w.N * (w.N - 1), cudaMemcpyDeviceToDevice,
                                 j->stream));
-    CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
-    launch_dgamma(w.tab, w.dg, w.N, w.X, w.counters, j->stream);
-    LAUNCHED(j, 2);
+    LAUNCHED(j, 1);
     j->has_tables = true;
     return RBX_OK;
 }
@@ -448,7 +459,11 @@ rbx_status rbx_get_tables(rbx_job *j, float *T, float *a, float *gam, uint8_t *K
         launch_get_tables(w.tab, T, a, gam, K, n, j->stream);
         LAUNCHED(j, 1);
     }
-    if (dg) CUDA_TRY(j, cudaMemcpyAsync(dg, w.dg, sizeof(float) * n, cudaMemcpyDeviceToDevice, j->stream));
+    if (dg) {
+        rbx_status st = ensure_dgamma(j);
+        if (st) return st;
+        CUDA_TRY(j, cudaMemcpyAsync(dg, w.dg, sizeof(float) * n, cudaMemcpyDeviceToDevice, j->stream));
+    }
     if (exits)
         CUDA_TRY(j, cudaMemcpyAsync(exits, w.exits, sizeof(float4) * (size_t)w.N * (w.N - 1), cudaMemcpyDeviceToDevice,
                                     j->stream));
@@ -536,11 +551,13 @@ rbx_status rbx_adjoint(rbx_job *j, double f, const void *R_dev, void *out_dev, i
     launch_symmetrize(static_cast<const float2 *>(R_dev), w.N, w.Rs, j->stream);
     LAUNCHED(j, 1);
     if (preconditioned && j->g.precision != RBX_FP32) {
-        launch_synth_bp_tc(w.tc, w.tab, w.dg, f, j->g.c0, j->stream);
+        launch_synth_bp_tc(w.tc, w.tab, f, j->g.c0, j->stream);
         launch_backproject_tc(w.tc, w.Rs, j->g.weight_mode, w.gpart, j->stream);
         launch_combine_adjoint(w.gpart, w.X, 0, j->g.weight_mode, 2.0, static_cast<float2 *>(out_dev), j->stream);
         LAUNCHED(j, 1);
     } else if (preconditioned) {
+        rbx_status st = ensure_dgamma(j);
+        if (st) return st;
         launch_synth_bp(w.tab, w.dg, w.N, w.X, f, j->g.c0, w.U, w.kap, j->stream);
         launch_backproject_simt(w.U, w.kap, w.Rs, w.N, w.X, 0, w.gpart, j->stream);
         launch_combine_adjoint(w.gpart, w.X, 0, j->g.weight_mode, 2.0, static_cast<float2 *>(out_dev), j->stream);
@@ -583,12 +600,13 @@ static rbx_status enqueue_freq(rbx_job *j, double f, double df, const float2 *da
     LAUNCHED(j, 2);
     if ((st = record(j, EV_RESID))) return st;
     if (j->g.precision != RBX_FP32) {
-        launch_synth_bp_tc(w.tc, w.tab, w.dg, f, j->g.c0, j->stream);
+        launch_synth_bp_tc(w.tc, w.tab, f, j->g.c0, j->stream);
         LAUNCHED(j, 1);
         if ((st = record(j, EV_SYNTH_B))) return st;
         launch_backproject_tc(w.tc, w.Rs, j->g.weight_mode, w.gpart, j->stream);
         LAUNCHED(j, 3);
     } else {
+        if ((st = ensure_dgamma(j))) return st;
         launch_synth_bp(w.tab, w.dg, w.N, w.X, f, j->g.c0, w.U, w.kap, j->stream);
         LAUNCHED(j, 1);
         if ((st = record(j, EV_SYNTH_B))) return st;
@@ -614,7 +632,7 @@ static rbx_status enqueue_update(rbx_job *j, double f, double df, const float2 *
     if ((st = enqueue_freq(j, f, df, data, 0))) return st;
     const int roff = residual_blocks(w.N) + 8;
     launch_snapshot(w.red + residual_blocks(w.N), w.red + roff + 3 * update_blocks(w.nx, w.ny), w.counters,
-                    w.tc.err, w.hist + (size_t)slot * kHistStride, j->stream);
+                    w.tc.err, (unsigned long long)w.N * w.X, w.hist + (size_t)slot * kHistStride, j->stream);
     LAUNCHED(j, 1);
     if ((st = record(j, EV_UPDATE))) return st;
     j->ns_valid = false;   // the model changed
@@ -772,8 +790,8 @@ rbx_status rbx_update_set(rbx_job *j, const double *freqs, int nf, double df, co
         launch_acc_scalar(w.red + nb, w.red + nb + 4, k == 0, j->stream);
         LAUNCHED(j, 1);
     }
-    launch_snapshot(w.red + nb + 4, w.red + roff + 3 * update_blocks(w.nx, w.ny), w.counters, w.tc.err, w.hist,
-                    j->stream);
+    launch_snapshot(w.red + nb + 4, w.red + roff + 3 * update_blocks(w.nx, w.ny), w.counters, w.tc.err,
+                    (unsigned long long)w.N * w.X, w.hist, j->stream);
     LAUNCHED(j, 1);
     if ((st = record(j, EV_UPDATE))) return st;
     j->ns_valid = false;

@@ -31,6 +31,27 @@ struct RayParams {
     int maxs;
 };
 
+// 1/v for v finite and away from 0 and the denormal range (a slowness, a triangle's edge
+// sum, an amplitude times a constant): the hardware approximation refined by one
+// Newton-Raphson step, r <- r + r (1 - v r).
+__device__ __forceinline__ float rcp_nr(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return fmaf(fmaf(-v, r, 1.f), r, r);
+}
+
+// Angular density (step a4): |d gamma / d e| Delta e as half the difference of the direction
+// angles of the two neighbouring transducers, wrapped to [-pi, pi). One expression for every
+// kernel that forms it, so they agree bit for bit.
+__device__ __forceinline__ float dgamma_of(float gam_next, float gam_prev)
+{
+    const float PI = 3.14159265358979f, TWO_PI = 6.28318530717959f, INV_TWO_PI = 0.159154943091895f;
+    float d = gam_next - gam_prev;
+    d = d - TWO_PI * floorf((d + PI) * INV_TWO_PI);
+    return 0.5f * fabsf(d);
+}
+
 // BF16 tensor-core operands of one job: planar complex planes, their TMA descriptors and
 // the back-projection partials (k_gemm_tc.cu).
 struct TcPlanes {
@@ -69,7 +90,7 @@ struct Workspace {
     float2 *data = nullptr;
     double *red = nullptr;           // reduction scratch
     double *hist = nullptr;          // [kHistSlots][kHistStride] per-update scalars
-    unsigned long long *counters = nullptr;   // [0] uncovered [1] clamped [2] bad rays [3] CAS bound [4] m <= 0 [5] bad model [6] mask count [7] uniform radius (float bits)
+    unsigned long long *counters = nullptr;   // [0] covered entries [1] clamped [2] bad rays [3] CAS bound [4] m <= 0 [5] bad model [6] mask count [7] uniform radius (float bits)
     int fwd_splits = 1;
     TcPlanes tc;
 };
@@ -101,11 +122,11 @@ void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_
 void launch_link_rays(const float *fields, const RayParams &p, const float4 *exits, int maxit, float4 *linked,
                       unsigned long long *counters, bool lossy, bool raw, cudaStream_t s);
 void launch_green_linked(const float4 *linked, int N, double f, double c0, float2 *g, cudaStream_t s);
-void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, unsigned long long *counters, cudaStream_t s);
+void launch_dgamma(const TabEntry *tab, float *dg, int N, int X, cudaStream_t s);
 void launch_direct_green(const float4 *exits, int N, double f, double c0, float2 *g, unsigned long long *counters,
                          cudaStream_t s);
 void launch_set_tables(const float *T, const float *a, const float *gam, const uint8_t *K, TabEntry *tab, size_t n,
-                       cudaStream_t s);
+                       unsigned long long *counters, cudaStream_t s);
 void launch_get_tables(const TabEntry *tab, float *T, float *a, float *gam, uint8_t *K, size_t n, cudaStream_t s);
 
 // k_gemm_simt.cu
@@ -134,7 +155,7 @@ int set_autotune(int mode);
 void tc_free(TcPlanes &p, cudaStream_t s);
 void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s);
 int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s);
-void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, const float *dg, double f, double c0, cudaStream_t s);
+void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, double f, double c0, cudaStream_t s);
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s);
 
 // k_update.cu
@@ -151,7 +172,7 @@ void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X
                    double df, double tau, double c0, float *c, double *red, unsigned long long *counters,
                    const Lossy &ab, double *acc, int mode, cudaStream_t s);
 void launch_snapshot(const double *r2, const double *upd3, const unsigned long long *counters, const unsigned *tc_err,
-                     double *slot, cudaStream_t s);
+                     unsigned long long n_entries, double *slot, cudaStream_t s);
 int residual_blocks(int N);
 int update_blocks(int nx, int ny);
 

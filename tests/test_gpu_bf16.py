@@ -148,3 +148,50 @@ def test_forward_split_autotuning():
         assert rel_l2(outs[2], outs[0]) <= 1e-5
     finally:
         rbx.autotune(prev)
+
+
+def holes_of(N, X, seed=5):
+    """Seeded uncovered entries: 3 % at random plus a quarter of the nodes of transducers on
+    both sides of every 32-transducer tile border and of the ring's wrap (0 and N - 1)."""
+    rng = np.random.default_rng(seed)
+    hole = rng.random((N, X)) < 0.03
+    rows = {0, N - 1} | {e for b in range(32, N, 32) for e in (b - 1, b)}
+    for e in rows:
+        hole[e, rng.choice(X, X // 4, replace=False)] = True
+    return hole
+
+
+@pytest.mark.parametrize("prec", [rbx.RBX_BF16, rbx.RBX_BF16X3])
+def test_backprojection_tables_with_holes(case, prec, oracle_mod):
+    """Uncovered entries (a = 0) zero the angular density of both neighbouring transducers
+    (step a4). The tensor-core operand synthesis forms that density itself inside
+    32-transducer tiles with one halo row on each side, wrapping around the ring, so holes sit
+    on tile borders and at the wrap. The back-projection matches the oracle's with the same
+    holes, the FP32 path's angular density array (rbx_get_tables) is the oracle's, and an
+    update reports exactly the injected number of uncovered entries."""
+    t = case.t32
+    assert case.tb.cov.all()
+    N, X = t["a"].shape
+    hole = holes_of(N, X)
+    a = np.where(hole, np.float32(0), t["a"])
+    o = oracle_mod.Oracle(case.g)
+    T, a64, gam = t["T"].astype(np.float64), a.astype(np.float64), t["gam"].astype(np.float64)
+    dg = o.dgamma(gam, (~hole).astype(np.int32))
+    assert (dg == 0).sum() > hole.sum()                     # holes also zero their neighbours
+    rng = np.random.default_rng(11)
+    R = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+    ref = o.backproject(case.f, T, a64, gam, t["K"].astype(np.int32), dg, R.astype(np.complex128))
+    data, _ = o.predict(case.f, case.w.c_true)
+    for p in (prec, rbx.RBX_FP32):
+        job = rbx.Job()
+        job.set_geometry(case.g, precision=p)
+        job.set_model(dev(case.c32))
+        job.set_tables(dev(t["T"]), dev(a), dev(t["gam"]), dev(t["K"], torch.uint8), dev(t["exits"]))
+        out = job.adjoint(case.f, dev(R, torch.complex64), True).cpu().numpy()
+        assert rel_l2(out, ref) <= (TOL[p] if p != rbx.RBX_FP32 else 1e-5)
+        dg_gpu = job.get_tables()["dg"].cpu().numpy()
+        assert np.abs(dg_gpu - dg).max() <= 2e-5
+        np.testing.assert_array_equal(dg_gpu == 0, dg == 0)
+        st = job.update_from_tables(case.f, 1e5, dev(data, torch.complex64))
+        assert st["n_uncovered"] == int(hole.sum())
+        job.close()

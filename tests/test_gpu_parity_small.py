@@ -124,6 +124,30 @@ def test_direct_green_identical_tables(which, request):
 
 
 @pytest.mark.parametrize("which", ["small", "ragged"])
+def test_direct_green_crossing_exits(which, request):
+    """Exit angles perturbed so that neighbouring rays cross (as past a caustic), with runs of
+    equal exit angles and, in some fans, a ray exiting just short of the transducer itself so
+    that its pair straddles the angle wrap: the GPU's first bracketing pair per receiver and
+    its interpolation match the oracle's linear scan over the pairs on the same exits."""
+    case = request.getfixturevalue(which)
+    t = case.oracle_tables32()
+    N = case.g.n_xducers
+    rng = np.random.default_rng(3)
+    ex = t["exits"].copy()
+    th = ex[..., 0].astype(np.float64) + rng.normal(0, 1.5 * 2 * math.pi / N, (N, N - 1))
+    th[:, 5:8] = th[:, 5:6]
+    for e in range(0, N, 4):
+        th[e, rng.integers(2, N - 3)] = 2 * math.pi * e / N - 1e-4
+    ex[..., 0] = np.angle(np.exp(1j * th)).astype(np.float32)
+    case.job.set_tables(dev(t["T"]), dev(t["a"]), dev(t["gam"]), dev(t["K"], torch.uint8), dev(ex))
+    for f in (2e5, 4e5):
+        g_gpu = case.job.direct_green(f).cpu().numpy()
+        g_orc, _ = case.o.direct_green(f, ex.astype(np.float64))
+        assert rel_l2(g_gpu, g_orc) <= 1e-5
+        assert np.abs(g_gpu - g_orc).max() <= 1e-4 * np.abs(g_orc).max()
+
+
+@pytest.mark.parametrize("which", ["small", "ragged"])
 def test_forward_identical_tables(which, request):
     case = request.getfixturevalue(which)
     t = case.inject()
@@ -233,6 +257,33 @@ def test_sweep_small(small):
     re1 = np.linalg.norm((c_gpu - w.c_true)[m]) / np.linalg.norm((w.geom.c0 - w.c_true)[m])
     assert re1 < re0
     small.job.set_model(dev(small.c32))
+
+
+@pytest.mark.parametrize("prec", [rbx.RBX_FP32, rbx.RBX_BF16])
+def test_uncovered_count_wide_mask(prec, oracle_mod):
+    """Mask out to 0.97 R (ragged ring of 50): nodes next to each transducer between the
+    tangent and its first ray stay uncovered. The count an update reports (the trace counts an
+    entry when its first triangle writes it) equals the number of a = 0 entries the tables
+    hold, and the covered sets of the CUDA path and the oracle agree but for entries within
+    rounding of a ray-tube edge."""
+    import dataclasses
+    w = P.custom(50, 83, 1e-3, 36e-3, kind="discs", ny=77, freqs=(3e5,))
+    g = dataclasses.replace(w.geom, mask_frac=0.97)
+    o = oracle_mod.Oracle(g)
+    c32 = w.c_init.astype(np.float32)
+    ns, f6 = o.fields_for(c32.astype(np.float64), 3e5)
+    tb = o.tables(f6)
+    assert tb.uncovered > 100
+    job = rbx.Job()
+    job.set_geometry(g, precision=prec)
+    job.set_model(dev(c32))
+    data, _ = o.predict(3e5, w.c_true)
+    st = job.update_frequency(3e5, 1e5, dev(data, torch.complex64))
+    gt = job.get_tables()
+    cov_g = gt["a"].cpu().numpy() > 0
+    assert st["n_uncovered"] == int((~cov_g).sum())
+    assert np.count_nonzero(cov_g != tb.cov.astype(bool)) <= 0.02 * tb.uncovered
+    job.close()
 
 
 def test_fixed_point_gpu(small):
