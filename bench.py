@@ -77,6 +77,7 @@ KERNEL_SRC = {
     "gemm_bp": ["k_gemm_tc.cu", "tc_sm100.cuh", "k_gemm_simt.cu"],
     "synth_fwd": ["k_gemm_tc.cu", "k_gemm_simt.cu"],
     "synth_bp": ["k_gemm_tc.cu", "k_gemm_simt.cu"],
+    "synth": ["k_gemm_tc.cu"],
 }
 
 
@@ -107,8 +108,12 @@ def algorithmic(kernel: str, N: int, X: int, precision: str):
         return 8.0 * N * (N + 1) / 2 * X, "flop", "alu" if precision == "fp32" else "tensor"
     if kernel == "trace":
         return 16.0 * NX + 16.0 * N * (N - 1), "byte", "hbm"
+    planes = 2.0 if precision == "bf16x3" else 1.0   # split BF16 writes a lo plane per hi plane
     if kernel == "synth_fwd":
-        return (16.0 + 8.0) * NX, "byte", "hbm"
+        return (16.0 + (8.0 * planes if precision != "fp32" else 8.0)) * NX, "byte", "hbm"
+    if kernel == "synth":
+        # fused: tables in once; forward (4 planes) and back-projection (6 planes) BF16 out
+        return (16.0 + 20.0 * planes) * NX, "byte", "hbm"
     if kernel == "synth_bp":
         # tables in; FP32: angular density in, U and kappa out; BF16: 6 planes out (x2 when split)
         out = {"fp32": 4.0 + 16.0, "bf16": 12.0, "bf16x3": 24.0}[precision]
@@ -579,6 +584,9 @@ def main():
     # per-kernel device time averaged over the timed steps; roofline of every kernel with an
     # algorithmic work figure, and of the dominant one
     kms = {k: float(np.mean([s["ms_kernel"][k] for s in stats])) for k in stats[0]["ms_kernel"]}
+    if args.precision != "fp32" and args.integration != "raw":
+        # one pass over the tables writes both contractions' operands (timed as the forward's)
+        kms["synth"] = kms.pop("synth_fwd") + kms.pop("synth_bp")
     dom = max(kms, key=kms.get)
     pk = peaks()
 

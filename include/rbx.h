@@ -81,12 +81,14 @@ typedef struct {
 
 /* indices into rbx_stats.ms_kernel */
 #define RBX_K_TRACE 0       /* ray trace + ray-to-grid scatter */
-#define RBX_K_SYNTH_FWD 1   /* Green's function synthesis for the forward */
+#define RBX_K_SYNTH_FWD 1   /* Green's function synthesis for the forward; in an update on the
+                               BF16 paths it also writes the back-projection's operands */
 #define RBX_K_GEMM_FWD 2    /* Born forward contraction */
-#define RBX_K_SYNTH_BP 3    /* reciprocal Green's function synthesis */
+#define RBX_K_SYNTH_BP 3    /* reciprocal Green's function synthesis (about 0 where
+                               RBX_K_SYNTH_FWD did it) */
 #define RBX_K_GEMM_BP 4     /* back-projection contraction with fused row-dot */
 #define RBX_K_FIELDS 5      /* smoothing + derivative fields */
-#define RBX_K_TABLES 6      /* table init, angular density, direct Green's function */
+#define RBX_K_TABLES 6      /* direct Green's function (+ angular density array, FP32) */
 #define RBX_K_UPDATE 7      /* residual + update */
 
 /* Create a job bound to a CUDA stream (a cudaStream_t; NULL means the legacy default

@@ -402,8 +402,12 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *_
 // The angular density dgamma (step a4) is formed here from the direction angles of the
 // neighbouring transducers: a 32-transducer tile reads one halo row on each side (rows wrap
 // around the ring), so the tables are read once more by 1/16 instead of a separate pass.
-__global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, int N, int X, int Npad, size_t pstride, float fhi,
-                              float flo, float C, __nv_bfloat16 *__restrict__ planes, int split)
+// With FWD the same pass also writes the forward's planes (those of k_synth_fwd_tc, from the
+// same phase): an update reads its tables once for both contractions' operands.
+template <bool FWD>
+__global__ void k_synth_tc(const TabEntry *__restrict__ tab, int N, int X, int Npad, size_t pstride, float fhi,
+                           float flo, float C, __nv_bfloat16 *__restrict__ planes, int split,
+                           const float2 *__restrict__ bw, int Xpad, size_t fpstride, __nv_bfloat16 *__restrict__ fplanes)
 {
     __shared__ float sv[6][32][33];
     __shared__ float sg[34][32];            // gamma of rows e0 - 1 .. e0 + 32 (mod N)
@@ -441,6 +445,7 @@ __global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, int N, int X, in
     for (int k = 0; k < 4; k++) {
         const int q = ty + 8 * k;
         float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float gr = 0.f, gi = 0.f;
         if (t[k].idk != kUncovered) {
             // slot q + 2 is row (e + 1) mod N and slot q row (e - 1) mod N, also for e = 0, N - 1
             const float dg = (sc[q + 2][tx] && sc[q][tx]) ? dgamma_of(sg[q + 2][tx], sg[q][tx]) : 0.f;
@@ -450,6 +455,8 @@ __global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, int N, int X, in
             sincospif(2.f * phase_cycles_tc(t[k].T, (int)(t[k].idk & 0xffu), fhi, flo), &sn, &cs);
             __sincosf(t[k].gam, &sgm, &cgm);
             const float A = dg * rcp_nr(C * t[k].a);
+            gr = C * t[k].a * cs;
+            gi = C * t[k].a * sn;
             float ur = A * cs, ui = -A * sn;
             v[0] = ur; v[1] = ui;
             v[2] = cgm * ur + sgm * ui; v[3] = cgm * ui - sgm * ur;   // conj(kappa) u
@@ -457,6 +464,16 @@ __global__ void k_synth_bp_tc(const TabEntry *__restrict__ tab, int N, int X, in
         }
 #pragma unroll
         for (int m = 0; m < 6; m++) sv[m][q][tx] = v[m];
+        if (FWD && e0 + q < N && x < X) {
+            // G and G v at [e][x], as k_synth_fwd_tc
+            const float2 vv = bw[x];   // Born weights of node x
+            const size_t o = (size_t)(e0 + q) * Xpad + x;
+            __nv_bfloat16 *lo = split ? fplanes + 4 * fpstride : nullptr;
+            put_split(fplanes + o, lo ? lo + o : nullptr, gr);
+            put_split(fplanes + fpstride + o, lo ? lo + fpstride + o : nullptr, gi);
+            put_split(fplanes + 2 * fpstride + o, lo ? lo + 2 * fpstride + o : nullptr, gr * vv.x - gi * vv.y);
+            put_split(fplanes + 3 * fpstride + o, lo ? lo + 3 * fpstride + o : nullptr, gr * vv.y + gi * vv.x);
+        }
     }
     __syncthreads();
     for (int q = ty; q < 32; q += 8) {
@@ -722,8 +739,17 @@ void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, double f, double c0, c
 {
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
-    k_synth_bp_tc<<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
-                                      static_cast<__nv_bfloat16 *>(p.bplanes), p.split);
+    k_synth_tc<false><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
+                                          static_cast<__nv_bfloat16 *>(p.bplanes), p.split, nullptr, 0, 0, nullptr);
+}
+
+void launch_synth_both_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s)
+{
+    float fhi = (float)f, flo = (float)(f - (double)fhi);
+    dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
+    k_synth_tc<true><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
+                                         static_cast<__nv_bfloat16 *>(p.bplanes), p.split, v, p.Xpad, p.fwd_pstride,
+                                         static_cast<__nv_bfloat16 *>(p.fplanes));
 }
 
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s)

@@ -67,14 +67,15 @@ __global__ __launch_bounds__(RB) void k_residual(const float2 *__restrict__ gdir
     if (threadIdx.x == 0) red[blockIdx.x] = s;
 }
 
-__global__ void k_final_sum(const double *__restrict__ part, int n, double *__restrict__ out)
+// Fixed-order sum of the block partials by one block: thread t adds partials t, t + RB, ...
+// in turn, then the block tree (the order depends on n only, so results repeat bit for bit).
+__global__ __launch_bounds__(RB) void k_final_sum(const double *__restrict__ part, int n, double *__restrict__ out)
 {
-    // one warp-free single thread: fixed order
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0;
-        for (int i = 0; i < n; i++) s += part[i];
-        *out = s;
-    }
+    __shared__ double sh[RB];
+    double v = 0;
+    for (int i = threadIdx.x; i < n; i += RB) v += part[i];
+    const double s = block_sum(v, sh);
+    if (threadIdx.x == 0) *out = s;
 }
 
 void launch_residual(const float2 *gdir, const float2 *D, const float2 *data, int N, float2 *R, float2 *Rs,
@@ -82,7 +83,7 @@ void launch_residual(const float2 *gdir, const float2 *D, const float2 *data, in
 {
     int nb = residual_blocks(N);
     k_residual<<<nb, RB, 0, s>>>(gdir, D, data, N, R, Rs, red);
-    k_final_sum<<<1, 32, 0, s>>>(red, nb, red + nb);
+    k_final_sum<<<1, RB, 0, s>>>(red, nb, red + nb);
 }
 
 __global__ void k_symmetrize(const float2 *__restrict__ R, int N, float2 *__restrict__ Rs)
@@ -210,15 +211,21 @@ __global__ __launch_bounds__(RB) void k_update(const float2 *__restrict__ gpart,
     }
 }
 
-__global__ void k_final_update(const double *__restrict__ red, int nb, double *__restrict__ out)
+// The update's three block partials (sum dc^2, max |dc|, sum dm^2) in the fixed order of
+// k_final_sum.
+__global__ __launch_bounds__(RB) void k_final_update(const double *__restrict__ red, int nb, double *__restrict__ out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s1 = 0, s2 = 0, s3 = 0;
-        for (int i = 0; i < nb; i++) {
-            s1 += red[i];
-            s2 = fmax(s2, red[nb + i]);
-            s3 += red[2 * nb + i];
-        }
+    __shared__ double sh[RB];
+    double s1 = 0, s2 = 0, s3 = 0;
+    for (int i = threadIdx.x; i < nb; i += RB) {
+        s1 += red[i];
+        s2 = fmax(s2, red[nb + i]);
+        s3 += red[2 * nb + i];
+    }
+    s1 = block_sum(s1, sh);
+    s2 = block_max(s2, sh);
+    s3 = block_sum(s3, sh);
+    if (threadIdx.x == 0) {
         out[0] = s1;
         out[1] = s2;
         out[2] = s3;
@@ -236,7 +243,7 @@ void launch_update(const float2 *gpart, const int *node2x, int nx, int ny, int X
     const double wy = ab.alpha0 ? pow(w, ab.y) : 0.0, tn = ab.alpha0 ? tan(PI * ab.y / 2) : 0.0;
     k_update<<<nb, RB, 0, s>>>(gpart, node2x, X, nx * ny, weight_mode == 0 ? -1.f : 1.f, pref / w, tau, (float)c0, c,
                                red, counters, ab.alpha0, w, ab.y, wy, tn, acc, mode);
-    k_final_update<<<1, 32, 0, s>>>(red, nb, red + 3 * nb);
+    k_final_update<<<1, RB, 0, s>>>(red, nb, red + 3 * nb);
 }
 
 }  // namespace rbx

@@ -483,12 +483,17 @@ rbx_status rbx_direct_green(rbx_job *j, double f, void *g_dev)
 }
 
 // D = sum_x G_r G_e v on the current tables, into w.D (symmetric).
-static rbx_status forward_core(rbx_job *j, double f, bool timed)
+// The Born forward on the current tables with the weights in w.v. With both (tensor-core
+// paths) the operand synthesis also writes the back-projection's planes for this frequency.
+static rbx_status forward_core(rbx_job *j, double f, bool timed, bool both = false)
 {
     Workspace &w = j->w;
     rbx_status st;
     if (j->g.precision != RBX_FP32) {
-        launch_synth_fwd_tc(w.tc, w.tab, w.v, f, j->g.c0, j->stream);
+        if (both)
+            launch_synth_both_tc(w.tc, w.tab, w.v, f, j->g.c0, j->stream);
+        else
+            launch_synth_fwd_tc(w.tc, w.tab, w.v, f, j->g.c0, j->stream);
         LAUNCHED(j, 1);
         if (timed && (st = record(j, EV_SYNTH_F))) return st;
         int splits = launch_forward_tc(w.tc, w.part, j->stream);
@@ -594,14 +599,16 @@ static rbx_status enqueue_freq(rbx_job *j, double f, double df, const float2 *da
     } else {
         launch_born_weights_rough(w.c, w.ns64, w.idx, w.X, f, j->g.dx * j->g.dx, lossy_of(j), w.v, j->stream);
         LAUNCHED(j, 1);
-        if ((st = forward_core(j, f, true))) return st;
+        if ((st = forward_core(j, f, true, true))) return st;
     }
     launch_residual(w.gdir, w.D, data, w.N, nullptr, w.Rs, w.red, j->stream);
     LAUNCHED(j, 2);
     if ((st = record(j, EV_RESID))) return st;
     if (j->g.precision != RBX_FP32) {
-        launch_synth_bp_tc(w.tc, w.tab, f, j->g.c0, j->stream);
-        LAUNCHED(j, 1);
+        if (j->raw) {   // otherwise the forward's synthesis wrote these planes
+            launch_synth_bp_tc(w.tc, w.tab, f, j->g.c0, j->stream);
+            LAUNCHED(j, 1);
+        }
         if ((st = record(j, EV_SYNTH_B))) return st;
         launch_backproject_tc(w.tc, w.Rs, j->g.weight_mode, w.gpart, j->stream);
         LAUNCHED(j, 3);
