@@ -34,8 +34,8 @@
  * Upsilon_m = omega c k~ (Eq. scattering-potential); the preconditioner's
  * |d|kbar|/d omega| carries the extra term y tan(pi y/2) omega^(y-1) alpha0.
  *
- * Readings where the paper is silent or ambiguous are listed in the design doc; the
- * ones that change arithmetic are restated beside the code below.
+ * Where the paper is silent or ambiguous, the reading taken is stated beside the
+ * code below that depends on it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1070,8 +1070,7 @@ static long state_direct_green(const og_geom *g, const og_state *s, double f, in
 
 /* Predicted data g = g_dir + F[m - m_s] on the current model (a5 + a7): the rays are
  * traced on the smoothed map and the rough part m - m_s, m_s = n_s^2, is carried by the
- * Born term. Reading: this is also the data model of the synthetic
- * workloads. stats: [0] uncovered entries, [1] rays not reaching the ring, [2] clamped pairs. */
+ * Born term. Reading: this is also the data model of the synthetic workloads. stats: [0] uncovered entries, [1] rays not reaching the ring, [2] clamped pairs. */
 void og_predict(const og_geom *g, double f, const double *c, double *out, double *stats)
 {
     og_state s;

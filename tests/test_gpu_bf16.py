@@ -1,6 +1,6 @@
 """BF16 and split-BF16 tensor-core paths (tcgen05) against the FP64 oracle.
 
-Tolerance (the benchmark spec): forward / back-projection relative L2 <= 5e-3 for BF16 on identical
+Tolerance (stated for the method): forward / back-projection relative L2 <= 5e-3 for BF16 on identical
 (oracle, FP32-rounded) tables; split BF16 (hi + lo, three products) keeps about 16 bits,
 tested at 2e-5; one update <= 0.05 m/s RMS from the oracle's."""
 import math

@@ -1,6 +1,6 @@
 """CUDA path against the FP64 oracle on small cases (element by element).
 
-Tolerances (north star, read per stage):
+Tolerances (stated for the method, read per stage):
   tables: T <= 1e-9 s absolute; a relative <= 1e-5; gamma <= 1e-5 rad; K exact; mask exact;
   forward / adjoint / direct Green's function on identical (oracle, FP32-rounded) tables:
   relative L2 <= 1e-5 (FP32 path);
