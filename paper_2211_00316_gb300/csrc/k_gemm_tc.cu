@@ -404,12 +404,14 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *_
 // around the ring), so the tables are read once more by 1/16 instead of a separate pass.
 // With FWD the same pass also writes the forward's planes (those of k_synth_fwd_tc, from the
 // same phase): an update reads its tables once for both contractions' operands.
-template <bool FWD>
-__global__ void k_synth_tc(const TabEntry *__restrict__ tab, int N, int X, int Npad, size_t pstride, float fhi,
-                           float flo, float C, __nv_bfloat16 *__restrict__ planes, int split,
-                           const float2 *__restrict__ bw, int Xpad, size_t fpstride, __nv_bfloat16 *__restrict__ fplanes)
+template <bool FWD, bool SPLIT>
+__global__ __launch_bounds__(256, 6) void k_synth_tc(const TabEntry *__restrict__ tab, int N, int X, int Npad,
+                                                     size_t pstride, float fhi, float flo, float C,
+                                                     __nv_bfloat16 *__restrict__ planes, const float2 *__restrict__ bw,
+                                                     int Xpad, size_t fpstride, __nv_bfloat16 *__restrict__ fplanes)
 {
-    __shared__ float sv[6][32][33];
+    constexpr int NPL = SPLIT ? 12 : 6;                      // back-projection planes (hi, then lo)
+    __shared__ __align__(16) __nv_bfloat16 sv[NPL][32][34];  // [plane][x][e]: rows of 17 words
     __shared__ float sg[34][32];            // gamma of rows e0 - 1 .. e0 + 32 (mod N)
     __shared__ unsigned char sc[34][32];    // covered flags of the same
     const int x0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
@@ -441,6 +443,8 @@ __global__ void k_synth_tc(const TabEntry *__restrict__ tab, int N, int X, int N
         sc[slot][tx] = h.idk != kUncovered;
     }
     __syncthreads();
+    float2 vv = make_float2(0.f, 0.f);
+    if (FWD && x < X) vv = bw[x];   // Born weights of node x
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int q = ty + 8 * k;
@@ -462,27 +466,36 @@ __global__ void k_synth_tc(const TabEntry *__restrict__ tab, int N, int X, int N
             v[2] = cgm * ur + sgm * ui; v[3] = cgm * ui - sgm * ur;   // conj(kappa) u
             v[4] = cgm * ur - sgm * ui; v[5] = cgm * ui + sgm * ur;   // kappa u
         }
+        // the tile transposed to [x][e] in shared memory, already rounded to BF16 (hi, lo)
 #pragma unroll
-        for (int m = 0; m < 6; m++) sv[m][q][tx] = v[m];
+        for (int m = 0; m < 6; m++) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v[m]);
+            sv[m][tx][q] = h;
+            if (SPLIT) sv[6 + m][tx][q] = __float2bfloat16_rn(v[m] - __bfloat162float(h));
+        }
         if (FWD && e0 + q < N && x < X) {
             // G and G v at [e][x], as k_synth_fwd_tc
-            const float2 vv = bw[x];   // Born weights of node x
             const size_t o = (size_t)(e0 + q) * Xpad + x;
-            __nv_bfloat16 *lo = split ? fplanes + 4 * fpstride : nullptr;
-            put_split(fplanes + o, lo ? lo + o : nullptr, gr);
-            put_split(fplanes + fpstride + o, lo ? lo + fpstride + o : nullptr, gi);
-            put_split(fplanes + 2 * fpstride + o, lo ? lo + 2 * fpstride + o : nullptr, gr * vv.x - gi * vv.y);
-            put_split(fplanes + 3 * fpstride + o, lo ? lo + 3 * fpstride + o : nullptr, gr * vv.y + gi * vv.x);
+            __nv_bfloat16 *lo = SPLIT ? fplanes + 4 * fpstride : nullptr;
+            put_split(fplanes + o, SPLIT ? lo + o : nullptr, gr);
+            put_split(fplanes + fpstride + o, SPLIT ? lo + fpstride + o : nullptr, gi);
+            put_split(fplanes + 2 * fpstride + o, SPLIT ? lo + 2 * fpstride + o : nullptr, gr * vv.x - gi * vv.y);
+            put_split(fplanes + 3 * fpstride + o, SPLIT ? lo + 3 * fpstride + o : nullptr, gr * vv.y + gi * vv.x);
         }
     }
     __syncthreads();
-    for (int q = ty; q < 32; q += 8) {
-        int xo = x0 + q, e = e0 + tx;
-        if (xo < X && e < N) {
-            size_t o = (size_t)xo * Npad + e;
+    // write-out: two neighbouring transducers per 32-bit store (Npad, e0 and the planes' base
+    // are even, so every store is aligned); entries past the last transducer are zero, as the
+    // padding must be
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(&sv[0][0][0]);
 #pragma unroll
-            for (int m = 0; m < 6; m++)
-                put_split(planes + m * pstride + o, split ? planes + (6 + m) * pstride + o : nullptr, sv[m][tx][q]);
+    for (int j = 0; j < 2; j++) {
+        const int item = threadIdx.x + 256 * j, xr = item >> 4, pr = item & 15;
+        if (x0 + xr < X) {
+            const size_t o = (size_t)(x0 + xr) * Npad + e0 + 2 * pr;
+#pragma unroll
+            for (int m = 0; m < NPL; m++)
+                *reinterpret_cast<uint32_t *>(planes + m * pstride + o) = sw[(m * 32 + xr) * 17 + pr];
         }
     }
 }
@@ -739,17 +752,28 @@ void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, double f, double c0, c
 {
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
-    k_synth_tc<false><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
-                                          static_cast<__nv_bfloat16 *>(p.bplanes), p.split, nullptr, 0, 0, nullptr);
+    __nv_bfloat16 *bp = static_cast<__nv_bfloat16 *>(p.bplanes);
+    const float C = green_const_tc(f, c0);
+    if (p.split)
+        k_synth_tc<false, true><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, nullptr, 0, 0,
+                                                   nullptr);
+    else
+        k_synth_tc<false, false><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, nullptr, 0,
+                                                    0, nullptr);
 }
 
 void launch_synth_both_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s)
 {
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
-    k_synth_tc<true><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
-                                         static_cast<__nv_bfloat16 *>(p.bplanes), p.split, v, p.Xpad, p.fwd_pstride,
-                                         static_cast<__nv_bfloat16 *>(p.fplanes));
+    __nv_bfloat16 *bp = static_cast<__nv_bfloat16 *>(p.bplanes), *fp = static_cast<__nv_bfloat16 *>(p.fplanes);
+    const float C = green_const_tc(f, c0);
+    if (p.split)
+        k_synth_tc<true, true><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, v, p.Xpad,
+                                                  p.fwd_pstride, fp);
+    else
+        k_synth_tc<true, false><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, v, p.Xpad,
+                                                   p.fwd_pstride, fp);
 }
 
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s)
