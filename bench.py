@@ -96,8 +96,8 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:k_trace_raster
     #     -s 2 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --serve-requests 0 (1 pass)
     ("precision_ring1024", "trace"): {"bytes": 2.518314240e9 + 2.457521152e9, "src": "24a6b04a0055"},
-    # same command, -k regex:"k_synth_tc|k_backproject_tc" -s 2 -c 2 (1 pass)
-    ("precision_ring1024", "synth"): {"bytes": 2.686406912e9 + 3.080937472e9, "src": "c3de7d29547c"},
+    # same command, -k regex:"k_synth_tc" -s 1 -c 1 (1 pass)
+    ("precision_ring1024", "synth"): {"bytes": 2.686410240e9 + 3.081414656e9, "src": "e37e0a2189d5"},
 }
 
 
