@@ -371,6 +371,11 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
     if (lo) *lo = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// G v with its rounding fixed (no contraction left to the compiler), so both kernels that
+// write the forward planes give the same bits
+__device__ __forceinline__ float gv_re(float gr, float gi, float2 v) { return __fmaf_rn(gr, v.x, -__fmul_rn(gi, v.y)); }
+__device__ __forceinline__ float gv_im(float gr, float gi, float2 v) { return __fmaf_rn(gr, v.y, __fmul_rn(gi, v.x)); }
+
 // planes [4][Npad][Xpad]: Gre, Gim, (G v)re, (G v)im (then 4 lo planes when split);
 // G_e[x] = C a exp(i 2 pi (f T - K/4 + 1/8))
 __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *__restrict__ v, int N, int X, int Xpad,
@@ -393,8 +398,8 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *_
     __nv_bfloat16 *lo = split ? planes + 4 * pstride : nullptr;
     put_split(planes + o, lo ? lo + o : nullptr, gr);
     put_split(planes + pstride + o, lo ? lo + pstride + o : nullptr, gi);
-    put_split(planes + 2 * pstride + o, lo ? lo + 2 * pstride + o : nullptr, gr * vv.x - gi * vv.y);
-    put_split(planes + 3 * pstride + o, lo ? lo + 3 * pstride + o : nullptr, gr * vv.y + gi * vv.x);
+    put_split(planes + 2 * pstride + o, lo ? lo + 2 * pstride + o : nullptr, gv_re(gr, gi, vv));
+    put_split(planes + 3 * pstride + o, lo ? lo + 3 * pstride + o : nullptr, gv_im(gr, gi, vv));
 }
 
 // planes [6][Xp][Npad] at [x][e]: u, conj(kappa) u, kappa u (re, im each);
@@ -479,8 +484,8 @@ __global__ __launch_bounds__(256, 6) void k_synth_tc(const TabEntry *__restrict_
             __nv_bfloat16 *lo = SPLIT ? fplanes + 4 * fpstride : nullptr;
             put_split(fplanes + o, SPLIT ? lo + o : nullptr, gr);
             put_split(fplanes + fpstride + o, SPLIT ? lo + fpstride + o : nullptr, gi);
-            put_split(fplanes + 2 * fpstride + o, SPLIT ? lo + 2 * fpstride + o : nullptr, gr * vv.x - gi * vv.y);
-            put_split(fplanes + 3 * fpstride + o, SPLIT ? lo + 3 * fpstride + o : nullptr, gr * vv.y + gi * vv.x);
+            put_split(fplanes + 2 * fpstride + o, SPLIT ? lo + 2 * fpstride + o : nullptr, gv_re(gr, gi, vv));
+            put_split(fplanes + 3 * fpstride + o, SPLIT ? lo + 3 * fpstride + o : nullptr, gv_im(gr, gi, vv));
         }
     }
     __syncthreads();

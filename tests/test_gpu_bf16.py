@@ -195,3 +195,17 @@ def test_backprojection_tables_with_holes(case, prec, oracle_mod):
         st = job.update_from_tables(case.f, 1e5, dev(data, torch.complex64))
         assert st["n_uncovered"] == int(hole.sum())
         job.close()
+
+
+@pytest.mark.parametrize("prec", [rbx.RBX_BF16, rbx.RBX_BF16X3])
+def test_update_synthesis_matches_forward_bits(case, prec):
+    """Data the job predicts on its own model leave a residual of exactly zero in an update:
+    the update's single synthesis pass (both contractions' operands) writes forward planes
+    bit-identical to those of the forward's own pass."""
+    job = case.jobs[prec]
+    job.set_model(dev(case.c32))
+    job.trace_rays(case.f)
+    data = job.predict(case.f)
+    st = job.update_from_tables(case.f, 1e5, data)
+    assert st["resid_norm2"] == 0.0
+    job.set_model(dev(case.c32))
