@@ -93,11 +93,11 @@ def kernel_src_hash(kernel: str) -> str:
 # DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (workload, kernel); valid only for the kernel sources they were taken on.
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum -k regex:k_trace_raster
-    #     -s 2 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --serve-requests 0 (1 pass)
-    ("precision_ring1024", "trace"): {"bytes": 2.518314240e9 + 2.457521152e9, "src": "24a6b04a0055"},
-    # same command, -k regex:"k_synth_tc" -s 1 -c 1 (1 pass)
-    ("precision_ring1024", "synth"): {"bytes": 2.686410240e9 + 3.081414656e9, "src": "e37e0a2189d5"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+    #     -k regex:"k_trace_raster|k_synth_tc" -s 3 -c 2 --csv
+    #     python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --serve-requests 0   (1 pass)
+    ("precision_ring1024", "trace"): {"bytes": 2.517364224e9 + 2.456158464e9, "src": "b452c39a3d19"},
+    ("precision_ring1024", "synth"): {"bytes": 2.686435328e9 + 3.078449664e9, "src": "d69c076ad855"},
 }
 
 

@@ -209,9 +209,13 @@ struct Maps6 {
 };
 
 // passes = 1: A_hi B_hi; passes = 3 (split BF16) adds A_hi B_lo and A_lo B_hi, and the
-// epilogue weights are read as hi + lo.
+// epilogue weights are read as hi + lo. With split BF16, as in the forward, no accumulation in
+// tensor memory runs over more than kSeg K chunks: the MMAs pause at each segment's end while
+// the epilogue adds that segment's row-dot into its registers (the row-dot is linear in P),
+// then restart from zero (one accumulator set, so the pause is not hidden; split BF16 only).
+template <bool SPLIT>
 __global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant__ Maps6 hi,
-                                                           const __grid_constant__ Maps6 lo, int passes,
+                                                           const __grid_constant__ Maps6 lo,
                                                            const __nv_bfloat16 *__restrict__ planes, size_t pstride,
                                                            int Npad, int nk, float sgn, float2 *__restrict__ bpart,
                                                            int Xp, unsigned *__restrict__ err)
@@ -220,14 +224,20 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant
     uint8_t *tiles = align1024(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)B_STAGES * B_TILES * TILE);
     uint64_t *empty = full + B_STAGES;
-    uint64_t *accb = empty + B_STAGES;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(accb + 1);
+    uint64_t *accb = empty + B_STAGES;     // accumulators of a segment ready to drain
+    uint64_t *accd = accb + 1;             // accumulators drained
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accd + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int et = blockIdx.x, xt = blockIdx.y;
+    constexpr int passes = SPLIT ? 3 : 1;
+    const int ntot = passes * nk;
+    const int seglen = SPLIT ? kSeg : ntot;
+    const int nseg = SPLIT ? (ntot + kSeg - 1) / kSeg : 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < B_STAGES; s++) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
         mbar_init(accb, 1);
+        mbar_init(accd, 128);
         fence_mbar_init();
     }
     if (warp == 1) tmem_alloc(tslot, 512);
@@ -239,7 +249,6 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant
     if (warp == 0 && lane == 0) {
         prefetch_tmap(&hi.ure); prefetch_tmap(&hi.uim); prefetch_tmap(&hi.vre); prefetch_tmap(&hi.vim);
         prefetch_tmap(&hi.rre); prefetch_tmap(&hi.rim);
-        const int ntot = passes * nk;
         int issued = 0;
         for (int c = 0; c < ntot; c++) {
             int s = c % B_STAGES;
@@ -263,8 +272,12 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant
         if (lane == 0) {
             const uint32_t ip = idesc_bf16(BM, BN, 0), in = idesc_bf16(BM, BN, 1);
             const uint32_t p0r = tmem, p0i = tmem + BN, p1r = tmem + 2 * BN, p1i = tmem + 3 * BN;
-            const int ntot = passes * nk;
             for (int c = 0; c < ntot; c++) {
+                const int seg = SPLIT ? c / kSeg : 0, cs = c - seg * seglen;
+                if (cs == 0 && seg >= 1) {   // the previous segment's accumulators have been read
+                    if (!mbar_wait(accd, (seg - 1) & 1)) { atomicOr(err, 32u); break; }
+                    fence_after();
+                }
                 int s = c % B_STAGES;
                 if (!mbar_wait(full + s, (c / B_STAGES) & 1)) { atomicOr(err, 2u); break; }
                 fence_after();
@@ -274,7 +287,7 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant
                     uint64_t ur = desc_sw128(base + k * 32), ui = desc_sw128(base + TILE + k * 32);
                     uint64_t vr = desc_sw128(base + 2 * TILE + k * 32), vi = desc_sw128(base + 3 * TILE + k * 32);
                     uint64_t rr = desc_sw128(base + 4 * TILE + k * 32), ri = desc_sw128(base + 5 * TILE + k * 32);
-                    uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                    uint32_t acc = (cs > 0 || k > 0) ? 1u : 0u;
                     mma_bf16(p0r, ur, rr, ip, acc);
                     mma_bf16(p0r, ui, ri, in, 1u);
                     mma_bf16(p0i, ur, ri, ip, acc);
@@ -285,18 +298,21 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant
                     mma_bf16(p1i, vi, rr, ip, 1u);
                 }
                 mma_commit(empty + s);
+                if (cs == seglen - 1 || c == ntot - 1) mma_commit(accb);
             }
-            mma_commit(accb);
-            if (!mbar_wait(accb, 0)) atomicOr(err, 8u);
+            // every MMA of this CTA has completed once the last segment is signalled
+            if (!mbar_wait(accb, (nseg - 1) & 1)) atomicOr(err, 8u);
         }
         __syncwarp();
     } else if (warp >= 2) {
         const int sub = warp & 3, row = sub * 32 + lane;
-        bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0));
-        fence_after();
         const int x = xt * BM + row;
         float gre = 0.f, gim = 0.f;
-        if (ok) {
+        bool ok = true;
+        for (int sg = 0; sg < nseg && ok; sg++) {
+            ok = __all_sync(0xffffffffu, mbar_wait(accb, sg & 1));
+            fence_after();
+            if (!ok) break;
             const uint32_t lanes = (uint32_t)(sub * 32) << 16;
             // epilogue weights at [x][e]: u (planes 0, 1) and kappa u (planes 4, 5); with
             // split BF16 the lo parts are planes 6 + (0, 1, 4, 5)
@@ -348,10 +364,13 @@ __global__ __launch_bounds__(192, 1) void k_backproject_tc(const __grid_constant
                     }
                 }
             }
-            bpart[(size_t)et * Xp + x] = make_float2(gre, gim);
-        } else if (lane == 0) {
-            atomicOr(err, 16u);
+            fence_before();
+            mbar_arrive(accd);
         }
+        if (ok)
+            bpart[(size_t)et * Xp + x] = make_float2(gre, gim);
+        else if (lane == 0)
+            atomicOr(err, 16u);
     }
     fence_before();
     __syncthreads();
@@ -630,7 +649,9 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t st)
     }
     if (!ok) return false;
     ok = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM) == cudaSuccess &&
-         cudaFuncSetAttribute(k_backproject_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM) ==
+         cudaFuncSetAttribute(k_backproject_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_backproject_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM) ==
              cudaSuccess;
     p.ready = ok;
     return ok;
@@ -789,9 +810,14 @@ void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float
     dim3 grd(p.Npad / BN, p.Xp / BM);
     Maps6 hi{p.bmaps[0][0], p.bmaps[0][1], p.bmaps[0][2], p.bmaps[0][3], p.bmaps[0][4], p.bmaps[0][5]};
     Maps6 lo{p.bmaps[1][0], p.bmaps[1][1], p.bmaps[1][2], p.bmaps[1][3], p.bmaps[1][4], p.bmaps[1][5]};
-    k_backproject_tc<<<grd, 192, B_SMEM, s>>>(hi, lo, p.split ? 3 : 1, static_cast<const __nv_bfloat16 *>(p.bplanes),
-                                              p.bp_pstride, p.Npad, p.Npad / BK, weight_mode == 0 ? -1.f : 1.f,
-                                              p.bpart, p.Xp, p.err);
+    const __nv_bfloat16 *bp = static_cast<const __nv_bfloat16 *>(p.bplanes);
+    const float sgn = weight_mode == 0 ? -1.f : 1.f;
+    if (p.split)
+        k_backproject_tc<true><<<grd, 192, B_SMEM, s>>>(hi, lo, bp, p.bp_pstride, p.Npad, p.Npad / BK, sgn, p.bpart,
+                                                        p.Xp, p.err);
+    else
+        k_backproject_tc<false><<<grd, 192, B_SMEM, s>>>(hi, lo, bp, p.bp_pstride, p.Npad, p.Npad / BK, sgn, p.bpart,
+                                                         p.Xp, p.err);
     k_bp_reduce<<<(p.X + 255) / 256, 256, 0, s>>>(p.bpart, p.Npad / BN, p.Xp, p.X, gpart);
 }
 

@@ -407,8 +407,10 @@ __global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict
             const bool last = xn * xn + yn * yn >= R2;
             if (last) {
                 // final partial step: crossing of the step's chord with the ring; the other
-                // quantities interpolated linearly along the chord
-                float b = x * dirx + y * diry, cc = x * x + y * y - R2;
+                // quantities interpolated linearly along the chord. A first step starts at the
+                // transducer, on the ring: |x|^2 - R^2 is 0 there, and its FP32 rounding residue
+                // (~R ulp(R)) would swamp b^2 for the near-tangent rays that end within a step
+                float b = x * dirx + y * diry, cc = i == 0 ? 0.f : x * x + y * y - R2;
                 float disc = b * b - cc;
                 float t = -b + sqrtf(disc > 0.f ? disc : 0.f);
                 t = fminf(fmaxf(t, 0.f), ds);
@@ -772,7 +774,8 @@ __device__ bool trace_one(const float *__restrict__ F, const RayParams &p, float
         float inc = hds * (F1.nr + F2.nr), incB = LOSSY ? hds * (F1.al + F2.al) : 0.f;
         const bool last = xn * xn + yn * yn >= R2;
         if (last) {
-            float b = x * dirx + y * diry, cc = x * x + y * y - R2;
+            // as in k_trace_raster: a first step starts on the ring (|x|^2 - R^2 = 0)
+            float b = x * dirx + y * diry, cc = i == 0 ? 0.f : x * x + y * y - R2;
             float disc = b * b - cc;
             float t = -b + sqrtf(disc > 0.f ? disc : 0.f);
             t = fminf(fmaxf(t, 0.f), ds);

@@ -1,0 +1,143 @@
+"""The largest ring the library takes: 4095 transducers, the limit of the 12-bit ray index in
+a table entry's ordering key, on a small grid (96 x 96 at 1 mm, ring radius 45 mm).
+
+The trace is compared with the oracle on sampled fans; the contractions run on identical
+closed-form water tables (T = s / c0, a = s^-1/2, gamma the direction from the transducer,
+K = 0; App. B) and are compared with the oracle's on sampled outputs; and sizes one past the
+limits are rejected with RBX_EINVAL.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2211_00316_gb300 import phantoms as P
+from paper_2211_00316_gb300 import rbx
+
+pytestmark = pytest.mark.gpu
+
+NMAX = 4095
+TOL = {rbx.RBX_FP32: 1e-5, rbx.RBX_BF16: 5e-3, rbx.RBX_BF16X3: 2e-5}
+
+
+def dev(x, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def wrap(d):
+    return np.angle(np.exp(1j * d))
+
+
+def geom(N=NMAX, **kw):
+    return P.Geometry(nx=96, ny=96, dx=1e-3, n_xducers=N, ring_radius=45e-3, **kw)
+
+
+def water_tables(g, idx):
+    """Closed-form tables of a uniform medium at c0 for every (transducer, mask node), and the
+    exit records (angle, T, a, K) of the fan rays: in water ray j of transducer e reaches
+    receiver e + j along the chord 2 R sin(pi j / N)."""
+    N, R, c0 = g.n_xducers, g.ring_radius, g.c0
+    Xg, Yg = g.coords()
+    px, py = Xg.ravel()[idx], Yg.ravel()[idx]
+    X = len(idx)
+    T = np.empty((N, X), np.float32)
+    a = np.empty_like(T)
+    gam = np.empty_like(T)
+    for e0 in range(0, N, 256):
+        b = 2 * np.pi * np.arange(e0, min(N, e0 + 256)) / N
+        dx = px[None, :] - R * np.cos(b)[:, None]
+        dy = py[None, :] - R * np.sin(b)[:, None]
+        s = np.hypot(dx, dy)
+        T[e0:e0 + len(b)] = s / c0
+        a[e0:e0 + len(b)] = 1.0 / np.sqrt(s)
+        gam[e0:e0 + len(b)] = np.arctan2(dy, dx)
+    j = np.arange(1, N)
+    chord = 2 * R * np.sin(np.pi * j / N)
+    ex = np.zeros((N, N - 1, 4), np.float32)
+    for e in range(N):
+        ex[e, :, 0] = wrap(2 * np.pi * (e + j) / N)
+    ex[..., 1] = (chord / c0)[None, :]
+    ex[..., 2] = (1.0 / np.sqrt(chord))[None, :]
+    return T, a, gam, np.zeros((N, X), np.uint8), ex
+
+
+@pytest.fixture(scope="module")
+def big_ring(oracle_mod):
+    g = geom()
+    o = oracle_mod.Oracle(g)
+    return g, o, water_tables(g, o.idx)
+
+
+def test_max_ring_trace_sampled_fans(big_ring, oracle_mod):
+    g, o, _ = big_ring
+    f = 3e5
+    c = np.full((g.ny, g.nx), g.c0)
+    ns, f6 = o.fields_for(c, f)
+    fans = np.array([0, 1, 2047, NMAX - 2, NMAX - 1], np.int32)
+    tb = o.tables(f6, fans=fans)
+    assert tb.uncovered == 0 and tb.bad_rays == 0
+    job = rbx.Job()
+    job.set_geometry(g, precision=rbx.RBX_BF16)
+    job.set_model(dev(c.astype(np.float32)))
+    job.trace_rays(f)
+    gt = job.get_tables()
+    sel = fans.tolist()
+    T, a, gam, K = (gt[k][sel].cpu().numpy() for k in ("T", "a", "gam", "K"))
+    assert np.all(a > 0)
+    assert np.abs(T - tb.T).max() <= 1e-9
+    assert np.abs(a / tb.a - 1).max() <= 1e-5
+    assert np.abs(wrap(gam - tb.gam)).max() <= 1e-5
+    np.testing.assert_array_equal(K.astype(np.int32), tb.K)
+    ex = gt["exits"][sel].cpu().numpy()
+    assert np.abs(ex[..., 1] - tb.exits[..., 1]).max() <= 1e-9
+    job.close()
+
+
+@pytest.mark.parametrize("prec", [rbx.RBX_FP32, rbx.RBX_BF16, rbx.RBX_BF16X3])
+def test_max_ring_contractions_identical_tables(big_ring, prec, oracle_mod):
+    g, o, (T, a, gam, K, ex) = big_ring
+    N, X = o.N, o.X
+    f = 3e5
+    job = rbx.Job()
+    job.set_geometry(g, precision=prec)
+    job.set_model(dev(np.full((g.ny, g.nx), g.c0, np.float32)))
+    job.set_tables(dev(T), dev(a), dev(gam), dev(K, torch.uint8), dev(ex))
+    rng = np.random.default_rng(4)
+    dm = (rng.standard_normal((g.ny, g.nx)) * 1e-9).astype(np.float32)
+    D = job.forward(f, dev(dm)).cpu().numpy()
+    w = 2 * math.pi * f
+    v = w * w * g.dx ** 2 * dm.astype(np.float64).ravel()[o.idx]
+    rows = np.array([0, 1, 1000, 2047, 3500, N - 2, N - 1])
+    Db = oracle_mod.forward_rows(o, f, T[rows].astype(np.float64), a[rows].astype(np.float64),
+                                 K[rows].astype(np.int32), v)
+    assert rel_l2(D[np.ix_(rows, rows)], Db) <= TOL[prec]
+    np.testing.assert_array_equal(D, D.T)
+    R = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+    out = job.adjoint(f, dev(R, torch.complex64), True).cpu().numpy()
+    nodes = np.linspace(0, X - 1, 40).astype(np.int64)
+    og = oracle_mod.Oracle(g)
+    og.X = len(nodes)
+    sub = {k: v[:, nodes] for k, v in (("T", T), ("a", a), ("gam", gam), ("K", K))}
+    dgn = og.dgamma(sub["gam"].astype(np.float64), np.ones((N, len(nodes)), np.int32))
+    ref = oracle_mod.backproject_nodes(og, f, sub["T"].astype(np.float64), sub["a"].astype(np.float64),
+                                       sub["gam"].astype(np.float64), sub["K"].astype(np.int32), dgn,
+                                       R.astype(np.complex128))
+    assert rel_l2(out[nodes], ref) <= TOL[prec]
+    job.close()
+
+
+def test_sizes_past_the_limits_are_rejected():
+    job = rbx.Job()
+    with pytest.raises(rbx.RbxError) as e:
+        job.set_geometry(geom(NMAX + 1))
+    assert e.value.status == 1
+    with pytest.raises(rbx.RbxError) as e:
+        job.set_geometry(geom(64, ds_frac=0.02))        # 2 R / ds = 4500 steps > 2047
+    assert e.value.status == 1
+    job.set_geometry(geom(64))                          # the job is still usable
+    job.close()
