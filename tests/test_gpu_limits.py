@@ -1,10 +1,12 @@
-"""The largest ring the library takes: 4095 transducers, the limit of the 12-bit ray index in
-a table entry's ordering key, on a small grid (96 x 96 at 1 mm, ring radius 45 mm).
+"""Size limits and degenerate sizes.
 
-The trace is compared with the oracle on sampled fans; the contractions run on identical
-closed-form water tables (T = s / c0, a = s^-1/2, gamma the direction from the transducer,
-K = 0; App. B) and are compared with the oracle's on sampled outputs; and sizes one past the
-limits are rejected with RBX_EINVAL.
+The largest ring the library takes: 4095 transducers, the limit of the 12-bit ray index in a
+table entry's ordering key, on a small grid (96 x 96 at 1 mm, ring radius 45 mm). The trace
+is compared with the oracle on sampled fans; the contractions run on identical closed-form
+water tables (T = s / c0, a = s^-1/2, gamma the direction from the transducer, K = 0;
+App. B) and are compared with the oracle's on sampled outputs. Sizes one past the limits are
+rejected with RBX_EINVAL. The smallest cases: a mask of one node (and an empty one, which is
+rejected) and a ring of 3 transducers.
 """
 import math
 
@@ -140,4 +142,73 @@ def test_sizes_past_the_limits_are_rejected():
         job.set_geometry(geom(64, ds_frac=0.02))        # 2 R / ds = 4500 steps > 2047
     assert e.value.status == 1
     job.set_geometry(geom(64))                          # the job is still usable
+    job.close()
+
+
+def disc_phantom(g, r=8e-3, dc=45.0):
+    X_, Y_ = g.coords()
+    return np.where(X_ ** 2 + Y_ ** 2 <= r * r, g.c0 + dc, g.c0)
+
+
+@pytest.mark.parametrize("prec", [rbx.RBX_FP32, rbx.RBX_BF16])
+def test_single_node_mask(prec, oracle_mod):
+    """The smallest mask: one grid node (odd grid, mask radius under one cell). A full update
+    from water matches the oracle's at that node, and the rest of the grid stays water; a mask
+    that holds no node (even grid, the centre between nodes) is rejected."""
+    g = P.Geometry(nx=97, ny=97, dx=1e-3, n_xducers=64, ring_radius=45e-3, mask_frac=0.4e-3 / 45e-3)
+    o = oracle_mod.Oracle(g)
+    assert o.X == 1
+    f, df = 3e5, 1e5
+    data, _ = o.predict(f, disc_phantom(g))
+    c_init = np.full((g.ny, g.nx), g.c0)
+    c_ref, st_ref, bad = o.update_frequency(f, df, c_init, data)
+    assert bad == 0
+    job = rbx.Job()
+    job.set_geometry(g, precision=prec)
+    job.set_model(dev(c_init.astype(np.float32)))
+    st = job.update_frequency(f, df, dev(data, torch.complex64))
+    c_gpu = job.get_model().cpu().numpy().astype(np.float64)
+    m = g.mask()
+    dc_ref = c_ref[m][0] - g.c0
+    assert abs(dc_ref) > 1.0                                     # the node moved (about 20 m/s)
+    # 0.05 m/s, or for BF16 the back-projection's relative bound (5e-3) of so large a step
+    tol = 0.05 if prec == rbx.RBX_FP32 else max(0.05, 5e-3 * abs(dc_ref))
+    assert abs(c_gpu[m][0] - c_ref[m][0]) <= tol
+    assert np.all(c_gpu[~m] == np.float32(g.c0))
+    assert st["n_uncovered"] == st_ref[4] == 0
+    with pytest.raises(rbx.RbxError) as e:
+        job.set_geometry(P.Geometry(nx=96, ny=96, dx=1e-3, n_xducers=64, ring_radius=45e-3,
+                                    mask_frac=0.4e-3 / 45e-3))
+    assert e.value.status == 1
+    job.close()
+
+
+@pytest.mark.parametrize("prec", [rbx.RBX_FP32, rbx.RBX_BF16])
+def test_smallest_ring(prec, oracle_mod):
+    """The smallest ring the library takes, 3 transducers: each fan is two rays and one ray
+    tube, so most (transducer, node) entries stay uncovered. The tables' covered entries
+    match the oracle's but for entries within rounding of a tube edge, and one update matches
+    the oracle's within 0.05 m/s RMS over the mask."""
+    g = P.Geometry(nx=97, ny=97, dx=1e-3, n_xducers=3, ring_radius=45e-3)
+    o = oracle_mod.Oracle(g)
+    f, df = 3e5, 1e5
+    c_init = np.full((g.ny, g.nx), g.c0)
+    ns, f6 = o.fields_for(c_init, f)
+    tb = o.tables(f6)
+    assert tb.uncovered > o.X                                    # most entries uncovered
+    data, _ = o.predict(f, disc_phantom(g))
+    c_ref, st_ref, bad = o.update_frequency(f, df, c_init, data)
+    job = rbx.Job()
+    job.set_geometry(g, precision=prec)
+    job.set_model(dev(c_init.astype(np.float32)))
+    st = job.update_frequency(f, df, dev(data, torch.complex64))
+    gt = job.get_tables()
+    cov = gt["a"].cpu().numpy() > 0
+    assert np.count_nonzero(cov != tb.cov.astype(bool)) <= 0.01 * o.X * 3
+    both = cov & tb.cov.astype(bool)
+    assert np.abs(gt["T"].cpu().numpy()[both] - tb.T[both]).max() <= 1e-9
+    assert st["n_uncovered"] == int((~cov).sum())
+    c_gpu = job.get_model().cpu().numpy().astype(np.float64)
+    m = g.mask()
+    assert np.sqrt(np.mean((c_gpu[m] - c_ref[m]) ** 2)) <= 0.05
     job.close()
