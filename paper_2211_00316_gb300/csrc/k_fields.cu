@@ -144,9 +144,12 @@ __global__ void k_fields(const double *__restrict__ ns, const double *__restrict
         nr = (float)(1.0 / (double)c_raw[k0] + tn * a0);
         if (as) al = (float)(wy * a0);
     }
-    float4 *o = reinterpret_cast<float4 *>(F + k0 * kFieldStride);
-    o[0] = make_float4((float)c, (float)fx, (float)fy, (float)fxx);
-    o[1] = make_float4((float)fxy, (float)fyy, al, nr);
+    const size_t nxy = (size_t)nx * ny;
+    float4 *o4 = reinterpret_cast<float4 *>(F);
+    float2 *o2 = reinterpret_cast<float2 *>(o4 + nxy);
+    o4[k0] = make_float4((float)c, (float)fx, (float)fy, (float)fxx);
+    o2[k0] = make_float2((float)fxy, (float)fyy);
+    o2[nxy + k0] = make_float2(al, nr);
 }
 
 void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *tmp64, double *ns64, float *ns,

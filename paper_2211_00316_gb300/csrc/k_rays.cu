@@ -16,8 +16,9 @@
 // id, K) and a 128-bit compare-and-swap keeps the smallest key, so the table does not
 // depend on the order in which warps finish. The ray samples are never stored.
 //
-// Fields are bilinearly interpolated from the 8-float-per-node field map (L1/L2 cached:
-// 8 MB at 512^2). Travel time uses compensated (Kahan) summation.
+// Fields are bilinearly interpolated from the field map (L1/L2 cached; a lossless trace on
+// the smoothed map reads 24 B per node, 6 MB at 512^2). Travel time uses compensated (Kahan)
+// summation.
 #include <climits>
 
 #include "rbx_internal.cuh"
@@ -45,10 +46,11 @@ __device__ __forceinline__ void field_eval(const float *__restrict__ F, const Ra
     float u = (px - p.x0) * p.inv_dx, v = (py - p.y0) * p.inv_dx;
     int i = clampi_((int)floorf(u), 0, p.nx - 2), j = clampi_((int)floorf(v), 0, p.ny - 2);
     float tx = u - (float)i, ty = v - (float)j;
-    const float4 *b = reinterpret_cast<const float4 *>(F) + ((size_t)j * p.nx + i) * 2;
-    const float4 *c = b + (size_t)p.nx * 2;
-    float4 a0 = __ldg(b), a1 = __ldg(b + 1), b0 = __ldg(b + 2), b1 = __ldg(b + 3);
-    float4 c0 = __ldg(c), c1 = __ldg(c + 1), d0 = __ldg(c + 2), d1 = __ldg(c + 3);
+    const size_t nxy = (size_t)p.nx * p.ny, k00 = (size_t)j * p.nx + i, k01 = k00 + p.nx;
+    const float4 *F4 = reinterpret_cast<const float4 *>(F);
+    const float2 *F2 = reinterpret_cast<const float2 *>(F4 + nxy);
+    float4 a0 = __ldg(F4 + k00), b0 = __ldg(F4 + k00 + 1), c0 = __ldg(F4 + k01), d0 = __ldg(F4 + k01 + 1);
+    float2 a1 = __ldg(F2 + k00), b1 = __ldg(F2 + k00 + 1), c1 = __ldg(F2 + k01), d1 = __ldg(F2 + k01 + 1);
     float w00 = (1.f - tx) * (1.f - ty), w10 = tx * (1.f - ty), w01 = (1.f - tx) * ty, w11 = tx * ty;
     o.n = w00 * a0.x + w10 * b0.x + w01 * c0.x + w11 * d0.x;
     o.gx = w00 * a0.y + w10 * b0.y + w01 * c0.y + w11 * d0.y;
@@ -56,8 +58,15 @@ __device__ __forceinline__ void field_eval(const float *__restrict__ F, const Ra
     o.hxx = w00 * a0.w + w10 * b0.w + w01 * c0.w + w11 * d0.w;
     o.hxy = w00 * a1.x + w10 * b1.x + w01 * c1.x + w11 * d1.x;
     o.hyy = w00 * a1.y + w10 * b1.y + w01 * c1.y + w11 * d1.y;
-    o.al = LOSSY ? w00 * a1.z + w10 * b1.z + w01 * c1.z + w11 * d1.z : 0.f;
-    o.nr = RAW ? w00 * a1.w + w10 * b1.w + w01 * c1.w + w11 * d1.w : o.n;
+    if (LOSSY || RAW) {
+        const float2 *F3 = F2 + nxy;
+        float2 a2 = __ldg(F3 + k00), b2 = __ldg(F3 + k00 + 1), c2 = __ldg(F3 + k01), d2 = __ldg(F3 + k01 + 1);
+        o.al = LOSSY ? w00 * a2.x + w10 * b2.x + w01 * c2.x + w11 * d2.x : 0.f;
+        o.nr = RAW ? w00 * a2.y + w10 * b2.y + w01 * c2.y + w11 * d2.y : o.n;
+    } else {
+        o.al = 0.f;
+        o.nr = o.n;
+    }
 }
 
 // A ray sample as a triangle vertex.
@@ -523,7 +532,11 @@ __global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsi
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.nx * p.ny) return;
-    const float4 u0 = F[0], u1 = F[1], a0 = F[2 * (size_t)k], a1 = F[2 * (size_t)k + 1];
+    const size_t nxy = (size_t)p.nx * p.ny;
+    const float2 *F2 = reinterpret_cast<const float2 *>(F + nxy), *F3 = F2 + nxy;
+    const float4 u0 = F[0], a0 = F[k];
+    const float2 v0 = F2[0], v1 = F3[0], b0 = F2[k], b1 = F3[k];
+    const float4 u1 = make_float4(v0.x, v0.y, v1.x, v1.y), a1 = make_float4(b0.x, b0.y, b1.x, b1.y);
     if (k == 0 && !(u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && u1.x == 0.f && u1.y == 0.f)) {
         atomicMax(ru, (unsigned long long)__float_as_uint(__int_as_float(0x7f800000)));
         return;

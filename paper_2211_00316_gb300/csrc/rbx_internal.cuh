@@ -8,7 +8,10 @@
 
 namespace rbx {
 
-constexpr int kFieldStride = 8;          // floats per node: n, n_x, n_y, n_xx, n_xy, n_yy, alpha, n_raw
+// Field map: 8 floats per node in three planes, so a lossless, smoothed trace touches only
+// the first two (24 B per node): [nxy] float4 (n, n_x, n_y, n_xx), [nxy] float2 (n_xy, n_yy),
+// [nxy] float2 (alpha, n_raw).
+constexpr int kFieldStride = 8;
 constexpr uint32_t kUncovered = 0xFFFFFFFFu;
 constexpr int kMaxSteps = 2047;          // ray samples index i < 2048 (11 bits of the key)
 constexpr int kMaxXducers = 4095;        // ray index j < 4096 (12 bits of the key)
