@@ -291,26 +291,32 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
     }
 }
 
+// Warps per block, each tracing the same rays of a neighbouring transducer; 20 warps per SM.
+constexpr int kFansPerBlock = 4;
+
 template <bool LOSSY, bool RAW>
-__global__ __launch_bounds__(128, 5) void k_trace_raster(const float *__restrict__ F, const int4 *__restrict__ rows_g,
+__global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trace_raster(const float *__restrict__ F, const int4 *__restrict__ rows_g,
                                                          TabEntry *__restrict__ tab, float4 *__restrict__ exits,
                                                          RayParams p, unsigned long long *counters)
 {
     const unsigned FULL = 0xffffffffu;
     extern __shared__ int4 rows[];                          // [ny] mask row ranges
-    __shared__ int q_xi[4][64];
-    __shared__ unsigned long long q_key[4][64];
-    __shared__ float4 q_v[4][64];
-    __shared__ unsigned q_cov[4];
+    __shared__ int q_xi[kFansPerBlock][64];
+    __shared__ unsigned long long q_key[kFansPerBlock][64];
+    __shared__ float4 q_v[kFansPerBlock][64];
+    __shared__ unsigned q_cov[kFansPerBlock];
     for (int q = threadIdx.x; q < p.ny; q += blockDim.x) rows[q] = rows_g[q];
-    if (threadIdx.x < 4) q_cov[threadIdx.x] = 0u;
+    if (threadIdx.x < kFansPerBlock) q_cov[threadIdx.x] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
-    const int e = blockIdx.y;
+    // the warps of a block trace the same 32 rays of neighbouring transducers: rotated by one
+    // ring step, those rays stay within about a cell of one another, so their field gathers
+    // share L1 lines
+    const int warp = blockIdx.x;
+    const int e = blockIdx.y * kFansPerBlock + wib;
     const int N = p.N;
     const int nwarps = (N - 2 + 30) / 31;
-    if (warp >= nwarps) return;  // whole warp leaves together
+    if (warp >= nwarps || e >= N) return;  // whole warp leaves together
     const int j = 1 + 31 * warp + lane;      // this lane's ray
     const bool has_ray = j <= N - 1;
     TabEntry *fan = tab + (size_t)e * p.X;
@@ -559,16 +565,16 @@ void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, f
                          unsigned long long *counters, bool lossy, bool raw, cudaStream_t s)
 {
     int nwarps = (p.N - 2 + 30) / 31;
-    dim3 grd((nwarps + 3) / 4, p.N);
+    dim3 grd(nwarps, (p.N + kFansPerBlock - 1) / kFansPerBlock);
     const size_t sm = (size_t)p.ny * sizeof(int4);
     if (lossy && raw)
-        k_trace_raster<true, true><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
+        k_trace_raster<true, true><<<grd, 32 * kFansPerBlock, sm, s>>>(fields, rows, tab, exits, p, counters);
     else if (lossy)
-        k_trace_raster<true, false><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
+        k_trace_raster<true, false><<<grd, 32 * kFansPerBlock, sm, s>>>(fields, rows, tab, exits, p, counters);
     else if (raw)
-        k_trace_raster<false, true><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
+        k_trace_raster<false, true><<<grd, 32 * kFansPerBlock, sm, s>>>(fields, rows, tab, exits, p, counters);
     else
-        k_trace_raster<false, false><<<grd, 128, sm, s>>>(fields, rows, tab, exits, p, counters);
+        k_trace_raster<false, false><<<grd, 32 * kFansPerBlock, sm, s>>>(fields, rows, tab, exits, p, counters);
 }
 
 // rows[iy] = (compact index of the row's first mask node, first ix, last ix); empty rows
