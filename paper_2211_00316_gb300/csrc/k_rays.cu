@@ -9,8 +9,9 @@
 // a final partial step that lands on the ring (Def. ray-parameterisation).
 //
 // GB300 mapping: one thread per ray, 32 adjacent rays of one fan per warp stepping in
-// lockstep; a block's four warps take the same rays of four neighbouring transducers. At each step a lane fetches its neighbour's new sample with a shuffle and
-// rasterises the ray-tube quad (rays j, j+1; samples i, i+1) as two triangles straight
+// lockstep; a block's four warps take the same rays of four neighbouring transducers. At
+// each step a lane fetches its neighbour's new sample with a shuffle and rasterises the
+// ray-tube quad (rays j, j+1; samples i, i+1) as two triangles straight
 // into the fan's table (Sec. 4.4: triangulation of the ray samples). Overlapping triangles
 // keep the first arrival: the 16-byte table entry starts with the key (T bits, triangle
 // id, K) and a 128-bit compare-and-swap keeps the smallest key, so the table does not
