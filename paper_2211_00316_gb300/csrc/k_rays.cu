@@ -832,85 +832,109 @@ __device__ bool trace_one(const float *__restrict__ F, const RayParams &p, float
     return false;
 }
 
-// Linked rays of the direct term (Sec. 4.4, Sec. 6.3.2): for each receiver r != e the
-// bracketing fan rays of k_direct_green start a secant iteration on the initial angle, kept
-// inside the bracket (regula falsi with the Illinois weighting), which stops when the exit lies
-// within tol radians of beta_r (at most maxit new rays); T and a are then interpolated in exit
-// angle between the two bracketing rays to beta_r exactly, K taken from the nearer; linked[e][r]
-// = (0, T, a, K) serves every frequency of the trace. Unbracketed receivers take the nearest
-// fan ray; those and the pairs that stopped on maxit are counted in counters[1].
-template <bool LOSSY, bool RAW>
-__global__ void k_link_rays(const float *__restrict__ F, RayParams p, const float4 *__restrict__ exits, int maxit,
-                            double tol, float4 *__restrict__ linked, unsigned long long *counters)
+// Linked rays of the direct term (Sec. 4.4, Sec. 6.3.2), in two kernels.
+//
+// Linking, step 1, one block per transducer: the first bracketing pair of fan rays of every
+// receiver (as in k_direct_green), or the nearest fan ray where none brackets it, kept in the
+// unused first slot of linked[e][r] as j (> 0) or -j; the diagonal is zeroed.
+__global__ void k_link_brackets(const float4 *__restrict__ exits, int N, float4 *__restrict__ linked)
 {
-    extern __shared__ float4 ex[];
-    const int N = p.N;
-    float *th = reinterpret_cast<float *>(ex + (N - 1));
+    extern __shared__ float4 ex_s[];
+    float *th = reinterpret_cast<float *>(ex_s);
     int *first = reinterpret_cast<int *>(th + (N - 1));
     const int e = blockIdx.x;
-    const double PI = 3.14159265358979323846, TWO_PI = 2.0 * PI;
-    const double step = TWO_PI / N, be = (double)e * step;
-    for (int q = threadIdx.x; q < N - 1; q += blockDim.x) {
-        float4 v = exits[(size_t)e * (N - 1) + q];
-        ex[q] = v;
-        th[q] = (float)wrap_turn((double)v.x - be);
-    }
+    const double step = 6.283185307179586476925 / N, be = (double)e * step;
+    for (int q = threadIdx.x; q < N - 1; q += blockDim.x)
+        th[q] = (float)wrap_turn((double)exits[(size_t)e * (N - 1) + q].x - be);
     __syncthreads();
     first_brackets(th, N, e, step, first);
-    const float xe = (float)(p.R * cos(be)), ye = (float)(p.R * sin(be));
-    auto rel = [&](double ang) { return wrap_turn(ang - be); };
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
-        if (r == e) { linked[(size_t)e * N + r] = make_float4(0.f, 0.f, 0.f, 0.f); continue; }
-        const double td = recv_rel(r, e, N, step);
-        const float t = (float)td;
-        const int found = first[r] == INT_MAX ? -1 : first[r];
-        double T, a;
-        int K;
-        if (found > 0) {
-            const float4 A = ex[found - 1], Bq = ex[found];
-            // bracketing secant (regula falsi, Illinois weighting): every new ray starts between
-            // the two bracketing rays, so it points inward like the fan's
-            double ga = be + PI / 2 + PI * found / N, gb = be + PI / 2 + PI * (found + 1) / N;
-            double fa = rel(A.x) - td, fb = rel(Bq.x) - td, wa = fa, wb = fb;
-            double Ta = A.y, Tb = Bq.y, aa = A.z, ab = Bq.z;
-            int Ka = (int)A.w, Kb = (int)Bq.w, it = 0, side = 0;
-            while (fabs(fa) > tol && fabs(fb) > tol && it < maxit && wb != wa) {
-                const double gc = (ga * wb - gb * wa) / (wb - wa);
-                float thc, Tc, ac;
-                int Kc;
-                if (!trace_one<LOSSY, RAW>(F, p, xe, ye, gc, thc, Tc, ac, Kc)) break;
-                double fc = rel(thc) - td;
-                if (fc > PI) fc -= TWO_PI;
-                if (fc < -PI) fc += TWO_PI;
-                it++;
-                if ((fc > 0) == (fb > 0)) {
-                    gb = gc; fb = fc; wb = fc; Tb = Tc; ab = ac; Kb = Kc;
-                    if (side == -1) wa *= 0.5;
-                    side = -1;
-                } else {
-                    ga = gc; fa = fc; wa = fc; Ta = Tc; aa = ac; Ka = Kc;
-                    if (side == 1) wb *= 0.5;
-                    side = 1;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r != e) {
+            int code = first[r];
+            if (code == INT_MAX) {
+                const float t = (float)recv_rel(r, e, N, step);
+                int best = 1;
+                float bd = 1e30f;
+                for (int j = 1; j <= N - 1; j++) {
+                    float d = fabsf(th[j - 1] - t);
+                    if (d < bd) { bd = d; best = j; }
                 }
+                code = -best;
             }
-            if (fabs(fa) > tol && fabs(fb) > tol) atomicAdd(&counters[1], 1ull);
-            const double fr = (fb == fa) ? 0.0 : -fa / (fb - fa);
-            T = Ta + fr * (Tb - Ta);
-            a = aa + fr * (ab - aa);
-            K = fabs(fa) <= fabs(fb) ? Ka : Kb;
-        } else {
-            int best = 1;
-            float bd = 1e30f;
-            for (int j = 1; j <= N - 1; j++) {
-                float d = fabsf(th[j - 1] - t);
-                if (d < bd) { bd = d; best = j; }
-            }
-            const float4 A = ex[best - 1];
-            T = A.y; a = A.z; K = (int)A.w;
-            atomicAdd(&counters[1], 1ull);
+            v.x = __int_as_float(code);
         }
-        linked[(size_t)e * N + r] = make_float4(0.f, (float)T, (float)a, (float)K);
+        linked[(size_t)e * N + r] = v;
     }
+}
+
+// Linking, step 2, one thread per (transducer, receiver) pair; a block's four warps take the
+// same 32 receiver offsets m = r - e of four neighbouring transducers, so their rays, rotated
+// by one ring step, share L1 lines. From the bracketing fan rays a secant on the initial
+// angle, kept inside the bracket (regula falsi with the Illinois weighting), stops when the
+// exit lies within tol radians of beta_r (at most maxit new rays); T and a are then
+// interpolated in exit angle between the two bracketing rays to beta_r exactly, K taken from
+// the nearer; linked[e][r] = (0, T, a, K) serves every frequency of the trace. Unbracketed
+// receivers take the nearest fan ray; those and the pairs that stopped on maxit are counted
+// in counters[1].
+template <bool LOSSY, bool RAW>
+__global__ __launch_bounds__(128, 4) void k_link_rays(const float *__restrict__ F, RayParams p,
+                                                   const float4 *__restrict__ exits, int maxit, double tol,
+                                                   float4 *__restrict__ linked, unsigned long long *counters)
+{
+    const int N = p.N;
+    const int e = blockIdx.y * 4 + (threadIdx.x >> 5), m = blockIdx.x * 32 + (threadIdx.x & 31) + 1;
+    if (e >= N || m > N - 1) return;
+    const int r = (e + m) % N;
+    const double PI = 3.14159265358979323846, TWO_PI = 2.0 * PI;
+    const double step = TWO_PI / N, be = (double)e * step;
+    const double td = (double)m * step;   // recv_rel(r, e, N, step)
+    float4 *slot = linked + (size_t)e * N + r;
+    const int code = __float_as_int(slot->x);
+    const float4 *ex = exits + (size_t)e * (N - 1);
+    auto rel = [&](double ang) { return wrap_turn(ang - be); };
+    double T, a;
+    int K;
+    if (code > 0) {
+        const int found = code;
+        const float xe = (float)(p.R * cos(be)), ye = (float)(p.R * sin(be));
+        const float4 A = ex[found - 1], Bq = ex[found];
+        // bracketing secant (regula falsi, Illinois weighting): every new ray starts between
+        // the two bracketing rays, so it points inward like the fan's
+        double ga = be + PI / 2 + PI * found / N, gb = be + PI / 2 + PI * (found + 1) / N;
+        double fa = rel(A.x) - td, fb = rel(Bq.x) - td, wa = fa, wb = fb;
+        double Ta = A.y, Tb = Bq.y, aa = A.z, ab = Bq.z;
+        int Ka = (int)A.w, Kb = (int)Bq.w, it = 0, side = 0;
+        while (fabs(fa) > tol && fabs(fb) > tol && it < maxit && wb != wa) {
+            const double gc = (ga * wb - gb * wa) / (wb - wa);
+            float thc, Tc, ac;
+            int Kc;
+            if (!trace_one<LOSSY, RAW>(F, p, xe, ye, gc, thc, Tc, ac, Kc)) break;
+            double fc = rel(thc) - td;
+            if (fc > PI) fc -= TWO_PI;
+            if (fc < -PI) fc += TWO_PI;
+            it++;
+            if ((fc > 0) == (fb > 0)) {
+                gb = gc; fb = fc; wb = fc; Tb = Tc; ab = ac; Kb = Kc;
+                if (side == -1) wa *= 0.5;
+                side = -1;
+            } else {
+                ga = gc; fa = fc; wa = fc; Ta = Tc; aa = ac; Ka = Kc;
+                if (side == 1) wb *= 0.5;
+                side = 1;
+            }
+        }
+        if (fabs(fa) > tol && fabs(fb) > tol) atomicAdd(&counters[1], 1ull);
+        const double fr = (fb == fa) ? 0.0 : -fa / (fb - fa);
+        T = Ta + fr * (Tb - Ta);
+        a = aa + fr * (ab - aa);
+        K = fabs(fa) <= fabs(fb) ? Ka : Kb;
+    } else {
+        const float4 A = ex[-code - 1];
+        T = A.y; a = A.z; K = (int)A.w;
+        atomicAdd(&counters[1], 1ull);
+    }
+    *slot = make_float4(0.f, (float)T, (float)a, (float)K);
 }
 
 // g[e][r] = C a exp(i 2 pi (f T - K/4 + 1/8)) from the linked rays' (-, T, a, K); 0 on the diagonal
@@ -937,19 +961,18 @@ void launch_green_linked(const float4 *linked, int N, double f, double c0, float
 void launch_link_rays(const float *fields, const RayParams &p, const float4 *exits, int maxit, float4 *linked,
                       unsigned long long *counters, bool lossy, bool raw, cudaStream_t s)
 {
-    size_t smem = (size_t)(p.N - 1) * (sizeof(float4) + sizeof(float)) + (size_t)p.N * sizeof(int);
+    const size_t smem = (size_t)(p.N - 1) * sizeof(float) + (size_t)p.N * sizeof(int);   // <= 33 KB
+    k_link_brackets<<<p.N, 256, smem, s>>>(exits, p.N, linked);
     const double tol = 1e-6;
-#define RBX_LINK(L, W)                                                                                   \
-    do {                                                                                                 \
-        if (smem > 48 * 1024)                                                                            \
-            cudaFuncSetAttribute(k_link_rays<L, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k_link_rays<L, W><<<p.N, 128, smem, s>>>(fields, p, exits, maxit, tol, linked, counters);          \
-    } while (0)
-    if (lossy && raw) RBX_LINK(true, true);
-    else if (lossy) RBX_LINK(true, false);
-    else if (raw) RBX_LINK(false, true);
-    else RBX_LINK(false, false);
-#undef RBX_LINK
+    const dim3 grd((p.N - 1 + 31) / 32, (p.N + 3) / 4);
+    if (lossy && raw)
+        k_link_rays<true, true><<<grd, 128, 0, s>>>(fields, p, exits, maxit, tol, linked, counters);
+    else if (lossy)
+        k_link_rays<true, false><<<grd, 128, 0, s>>>(fields, p, exits, maxit, tol, linked, counters);
+    else if (raw)
+        k_link_rays<false, true><<<grd, 128, 0, s>>>(fields, p, exits, maxit, tol, linked, counters);
+    else
+        k_link_rays<false, false><<<grd, 128, 0, s>>>(fields, p, exits, maxit, tol, linked, counters);
 }
 
 // ---------------------------------------------------------------- table I/O
