@@ -96,7 +96,7 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:"k_trace_raster|k_synth_tc" -s 3 -c 2 --csv
     #     python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --serve-requests 0   (1 pass)
-    ("precision_ring1024", "trace"): {"bytes": 2.519553024e9 + 2.463698176e9, "src": "2bc28558174a"},
+    ("precision_ring1024", "trace"): {"bytes": 2.519553024e9 + 2.463698176e9, "src": "28fa90b05204"},
     ("precision_ring1024", "synth"): {"bytes": 2.686435328e9 + 3.078449664e9, "src": "d69c076ad855"},
 }
 
