@@ -504,6 +504,7 @@ def main():
         job = rbx.Job(stream)
         job.set_geometry(g, precision=prec)
         N, X = job.N, job.X
+        tuning = job.tuning() if args.precision != "fp32" else None
         if args.absorption:
             job.set_absorption(torch.tensor(P.absorption_map(w.c_true), dtype=torch.float32, device="cuda"), 1.4)
         if args.integration == "raw":
@@ -628,7 +629,8 @@ def main():
                        "absorption": ("breast map 0-1 dB/(MHz^1.4 cm), y=1.4" if args.absorption else "none"),
                        "integration": args.integration, "frequencies_per_update": K, "linking": args.link,
                        "l2": "inputs larger than L2 (tables N*X*16 B = %.2f GB)" % (16.0 * N * X / 1e9),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "forward_k_split": tuning},
             "gpu_launches": int(sum(s["n_launches"] for s in stats)),
             "clocks": clk, "e2e": e2e, "roofline": roof, "rooflines": roofs,
             "kernel_ms": kms, "stage_ms": {k: float(np.mean([s[k] for s in stats]))
