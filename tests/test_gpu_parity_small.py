@@ -286,6 +286,35 @@ def test_uncovered_count_wide_mask(prec, oracle_mod):
     job.close()
 
 
+def test_caustics_in_a_slow_lens(oracle_mod):
+    """A strong slow Gaussian lens, c = 1500 / (1 + 0.25 exp(-r^2 / (8 mm)^2)), focuses the rays
+    through it: the central rays of every fan pass a caustic before they reach the ring (the
+    oracle's sign change of J is pinned against an independent ray integration in
+    test_oracle_caustic.py). The caustic counts K of the CUDA path match the oracle's in the
+    exit records and in the tables (first arrivals, so few table entries carry K = 1), and the
+    travel times agree within the usual 1e-9 s."""
+    g = P.Geometry(nx=96, ny=96, dx=1e-3, n_xducers=64, ring_radius=45e-3)
+    X, Y = g.coords()
+    c32 = (1500.0 / (1 + 0.25 * np.exp(-(X ** 2 + Y ** 2) / (8e-3) ** 2))).astype(np.float32)
+    f = 1e6
+    o = oracle_mod.Oracle(g)
+    ns, f6 = o.fields_for(c32.astype(np.float64), f)
+    tb = o.tables(f6)
+    assert tb.bad_rays == 0 and (tb.exits[..., 3] > 0).sum() >= 64 and (tb.K > 0).sum() > 0
+    job = rbx.Job()
+    job.set_geometry(g)
+    job.set_model(dev(c32))
+    job.trace_rays(f)
+    gt = {k: v.cpu().numpy() for k, v in job.get_tables().items()}
+    np.testing.assert_array_equal(gt["exits"][..., 3], tb.exits[..., 3].astype(np.float32))
+    cov = gt["a"] > 0
+    np.testing.assert_array_equal(cov, tb.cov.astype(bool))
+    np.testing.assert_array_equal(gt["K"].astype(np.int32)[cov], tb.K[cov])
+    assert np.abs(gt["T"] - tb.T)[cov].max() <= 1e-9
+    assert np.abs(gt["exits"][..., 1] - tb.exits[..., 1]).max() <= 1e-9
+    job.close()
+
+
 def test_fixed_point_gpu(small):
     """Data predicted by the GPU's own model give a zero residual and no update."""
     f = small.f
