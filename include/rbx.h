@@ -334,6 +334,16 @@ rbx_status rbx_get_tuning(const rbx_job *job, int *fwd_splits, int *candidates_t
  * reserve to the device (after synchronising the device). Either pointer may be NULL. */
 rbx_status rbx_pool_usage(size_t *used, size_t *reserved, int trim);
 
+/* Diagnostic of the failure handling (the paper has no counterpart). Every wait of the
+ * tensor-core kernels on a barrier or a copy is bounded: after about one second of spinning
+ * the kernel records a timeout, stops and frees what it holds, and the call returns
+ * RBX_ETIMEOUT. This runs one kernel on the current device whose single thread waits, with
+ * that same bound, on a barrier that nothing ever signals. *timed_out = 1 when the wait gave
+ * up as it should (the expected result), 0 if the barrier completed. The call allocates and
+ * frees 4 bytes of device memory, synchronises the device, takes about one second and leaves
+ * the CUDA context usable. */
+rbx_status rbx_selftest_bounded_wait(int *timed_out);
+
 /* Wait for all work queued on the job's stream. */
 rbx_status rbx_synchronize(rbx_job *job);
 

@@ -802,6 +802,23 @@ void launch_synth_both_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, dou
                                                    p.fwd_pstride, fp);
 }
 
+// One thread waits, with the bound every tensor-core kernel uses, on an mbarrier that nothing
+// signals: flag = 1 when the wait gave up.
+__global__ void k_wait_selftest(unsigned *flag)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        *flag = mbar_wait(&bar, 0) ? 0u : 1u;
+    }
+}
+
+void launch_wait_selftest(unsigned *flag, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(flag);
+}
+
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s)
 {
     size_t nn = (size_t)p.N * p.N;

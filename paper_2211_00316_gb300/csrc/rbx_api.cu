@@ -1017,6 +1017,28 @@ rbx_status rbx_get_tuning(const rbx_job *j, int *fwd_splits, int *candidates_tim
     return RBX_OK;
 }
 
+rbx_status rbx_selftest_bounded_wait(int *timed_out)
+{
+    if (!timed_out) return RBX_EINVAL;
+    *timed_out = 0;
+    unsigned *flag = nullptr, h = 0;
+    if (cudaMalloc(&flag, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return RBX_ENOMEM;
+    }
+    rbx_status st = RBX_OK;
+    if (cudaMemset(flag, 0, sizeof(unsigned)) != cudaSuccess) st = RBX_ECUDA;
+    if (st == RBX_OK) {
+        launch_wait_selftest(flag, 0);
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(&h, flag, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = RBX_ECUDA;
+    }
+    cudaFree(flag);
+    if (st == RBX_OK) *timed_out = h == 1u ? 1 : 0;
+    return st;
+}
+
 rbx_status rbx_pool_usage(size_t *used, size_t *reserved, int trim)
 {
     int dev = 0;

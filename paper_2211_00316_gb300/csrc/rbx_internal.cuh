@@ -159,6 +159,8 @@ void tc_free(TcPlanes &p, cudaStream_t s);
 void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s);
 int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s);
 void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, double f, double c0, cudaStream_t s);
+// a bounded wait on a barrier nothing signals (flag = 1 when it gave up)
+void launch_wait_selftest(unsigned *flag, cudaStream_t s);
 // both operand sets of an update in one pass over the tables (forward planes with weights v)
 void launch_synth_both_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s);
 void launch_backproject_tc(TcPlanes &p, const float2 *Rs, int weight_mode, float2 *gpart, cudaStream_t s);

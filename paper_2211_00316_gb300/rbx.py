@@ -86,6 +86,7 @@ _SIGS = {
     "rbx_set_linking": [_P, C.c_int],
     "rbx_update_set": [_P, C.POINTER(C.c_double), C.c_int, C.c_double, _P, C.POINTER(Stats)],
     "rbx_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "rbx_selftest_bounded_wait": [C.POINTER(C.c_int)],
     "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
     "rbx_server_times": [_P, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "rbx_server_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
@@ -102,6 +103,16 @@ def exported_symbols() -> list[str]:
 def autotune(mode: int = -1) -> int:
     """Set (0 heuristic, 1 autotune) or query (-1) the forward split autotuning; returns the previous mode."""
     return int(load().rbx_autotune(int(mode)))
+
+
+def selftest_bounded_wait() -> bool:
+    """Run the bounded-wait diagnostic (rbx_selftest_bounded_wait): True when a wait on a barrier
+    that nothing signals gave up after the library's bound, as it must."""
+    t = C.c_int()
+    st = load().rbx_selftest_bounded_wait(C.byref(t))
+    if st != 0:
+        raise RbxError(st, "rbx_selftest_bounded_wait failed")
+    return bool(t.value)
 
 
 def pool_usage(trim: bool = False) -> dict:
