@@ -551,6 +551,13 @@ def main():
         torch.cuda.synchronize()
         clk = clocks.stop()
         ms = ev0.elapsed_time(ev1)
+        # image quality after the timed updates: RE of Sec. 6.4 on the mask, in percent
+        m = g.mask()
+        ct = np.asarray(w.c_true, dtype=np.float64)[m]
+        den = np.linalg.norm(g.c0 - ct)
+        re = {"initial": float(np.linalg.norm(np.asarray(w.c_init, np.float64)[m] - ct) / den * 100),
+              "after_timed_updates": float(np.linalg.norm(job.get_model().cpu().numpy().astype(np.float64)[m] - ct)
+                                           / den * 100)}
         ms = REP.max_over_ranks(ms, "cuda")
         if world > 1:
             dist.barrier()
@@ -635,7 +642,8 @@ def main():
             "clocks": clk, "e2e": e2e, "roofline": roof, "rooflines": roofs,
             "kernel_ms": kms, "stage_ms": {k: float(np.mean([s[k] for s in stats]))
                                            for k in ("ms_trace", "ms_forward", "ms_backproj", "ms_total")},
-            "n_uncovered": int(stats[-1]["n_uncovered"]), "rms_dc_last": stats[-1]["rms_dc"]}
+            "n_uncovered": int(stats[-1]["n_uncovered"]), "rms_dc_last": stats[-1]["rms_dc"],
+            "relative_error_percent": re}
     if serve is not None:
         line["latency"] = {"p50_s": serve["open_loop"]["p50_s"], "p99_s": serve["open_loop"]["p99_s"],
                            "requests": serve["requests"], "rate_req_s": serve["rate_req_s"],
