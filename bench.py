@@ -469,6 +469,8 @@ def main():
                     help="secant ray linking of the direct term, new rays per pair (rbx_set_linking; 0: off)")
     ap.add_argument("--set-size", type=int, default=1,
                     help="frequencies per update (rbx_update_set); value then counts frequencies per second")
+    ap.add_argument("--log-jsonl", default=None,
+                    help="append one JSON line per timed update (frequency, residual, model change, stage times)")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="default workload: requests of the short served run reported beside throughput (0 = none)")
     args = ap.parse_args()
@@ -551,6 +553,11 @@ def main():
         torch.cuda.synchronize()
         clk = clocks.stop()
         ms = ev0.elapsed_time(ev1)
+        if args.log_jsonl and rank == 0:
+            with open(args.log_jsonl, "a") as fh:
+                for k, st in zip(range(args.warmup, total_steps), stats):
+                    fq = [float(w.freqs[q]) for q in fset[k]] if K > 1 else float(w.freqs[fidx[k]])
+                    fh.write(json.dumps({"step": k, "freq_hz": fq, **st}) + "\n")
         # image quality after the timed updates: RE of Sec. 6.4 on the mask, in percent
         m = g.mask()
         ct = np.asarray(w.c_true, dtype=np.float64)[m]
