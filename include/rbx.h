@@ -220,6 +220,14 @@ rbx_status rbx_update_frequency_async(rbx_job *job, double freq_hz, double dfreq
  * (RBX_ENUMERIC, RBX_ETIMEOUT, ...). */
 rbx_status rbx_get_stats(rbx_job *job, int slot, rbx_stats *out);
 
+/* With on != 0, every later rbx_update_frequency_async records its stage events into the
+ * events of its own stats slot (64 sets, created by this call), so rbx_get_stats also
+ * returns that update's device timings (ms_trace, ms_forward, ms_backproj, ms_total,
+ * ms_kernel) and its launch count, as rbx_update_frequency does. A slot's timings are those
+ * of the last update queued into it. on == 0 frees the events (after waiting for the job's
+ * stream). */
+rbx_status rbx_set_slot_timing(rbx_job *job, int on);
+
 /* Batched form: the full low-to-high sweeps of n independent jobs (slices of different
  * sizes), freqs[i][0..nf[i]-1] with data_dev[i] holding nf[i] N_i x N_i blocks, nf[i] <= 64.
  * Each job's sweep runs on a stream of its own, forked from and joined to one origin stream;

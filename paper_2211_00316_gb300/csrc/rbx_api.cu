@@ -35,6 +35,9 @@ struct rbx_job {
     int *d_count = nullptr;
     std::string err;
     cudaEvent_t ev[EV_COUNT]{};
+    cudaEvent_t *evp = nullptr;         // the event set record() writes: ev, or a slot's set
+    cudaEvent_t *slot_ev = nullptr;     // [kHistSlots][EV_COUNT] (rbx_set_slot_timing)
+    long long slot_launches[kHistSlots] = {};
     long long launches = 0;
 };
 
@@ -114,13 +117,16 @@ static int max_steps(const rbx_geometry &g) { return (int)std::ceil(3.0 * g.ring
 static float elapsed(const rbx_job *j, int a, int b)
 {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, j->ev[a], j->ev[b]) != cudaSuccess) return 0.f;
+    if (cudaEventElapsedTime(&ms, j->evp[a], j->evp[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
     return ms;
 }
 
 static rbx_status record(rbx_job *j, int k)
 {
-    CUDA_TRY(j, cudaEventRecord(j->ev[k], j->stream));
+    CUDA_TRY(j, cudaEventRecord(j->evp[k], j->stream));
     return RBX_OK;
 }
 
@@ -133,6 +139,7 @@ rbx_status rbx_create(rbx_job **out, void *cuda_stream)
     rbx_job *j = new (std::nothrow) rbx_job();
     if (!j) return RBX_ENOMEM;
     j->stream = static_cast<cudaStream_t>(cuda_stream);   // NULL: the legacy default stream
+    j->evp = j->ev;
     for (int k = 0; k < EV_COUNT; k++) {
         if (cudaEventCreate(&j->ev[k]) != cudaSuccess) {
             rbx_destroy(j);
@@ -152,6 +159,11 @@ rbx_status rbx_destroy(rbx_job *j)
     cudaStreamSynchronize(j->stream);
     for (int k = 0; k < EV_COUNT; k++)
         if (j->ev[k]) cudaEventDestroy(j->ev[k]);
+    if (j->slot_ev) {
+        for (int k = 0; k < kHistSlots * EV_COUNT; k++)
+            if (j->slot_ev[k]) cudaEventDestroy(j->slot_ev[k]);
+        delete[] j->slot_ev;
+    }
     delete j;
     return RBX_OK;
 }
@@ -830,9 +842,41 @@ rbx_status rbx_update_frequency_async(rbx_job *j, double f, double df, const voi
     NEED(j, j->has_geom, RBX_ESTATE, "rbx_update_frequency_async before rbx_set_geometry");
     NEED(j, !bad_freq(f) && std::isfinite(df) && df > 0, RBX_EINVAL, "frequency and spacing must be finite and > 0");
     NEED(j, slot >= 0 && slot < kHistSlots, RBX_EINVAL, "stats slot must be in [0, 64)");
+    const long long l0 = j->launches;
+    if (j->slot_ev) j->evp = j->slot_ev + (size_t)slot * EV_COUNT;   // this update's own events
     rbx_status st = rbx_trace_rays(j, f);
-    if (st) return st;
-    return enqueue_update(j, f, df, static_cast<const float2 *>(data_dev), true, slot);
+    if (!st) st = enqueue_update(j, f, df, static_cast<const float2 *>(data_dev), true, slot);
+    j->evp = j->ev;
+    j->slot_launches[slot] = j->launches - l0;
+    return st;
+}
+
+rbx_status rbx_set_slot_timing(rbx_job *j, int on)
+{
+    if (!j) return RBX_EINVAL;
+    if (!on) {
+        if (j->slot_ev) {
+            CUDA_TRY(j, cudaStreamSynchronize(j->stream));
+            for (int k = 0; k < kHistSlots * EV_COUNT; k++)
+                if (j->slot_ev[k]) cudaEventDestroy(j->slot_ev[k]);
+            delete[] j->slot_ev;
+            j->slot_ev = nullptr;
+        }
+        return RBX_OK;
+    }
+    if (j->slot_ev) return RBX_OK;
+    j->slot_ev = new (std::nothrow) cudaEvent_t[(size_t)kHistSlots * EV_COUNT]();
+    if (!j->slot_ev) return fail(j, RBX_ENOMEM, "host allocation of the slot events failed");
+    for (int k = 0; k < kHistSlots * EV_COUNT; k++) {
+        if (cudaEventCreate(&j->slot_ev[k]) != cudaSuccess) {
+            cudaGetLastError();
+            for (int q = 0; q < k; q++) cudaEventDestroy(j->slot_ev[q]);
+            delete[] j->slot_ev;
+            j->slot_ev = nullptr;
+            return fail(j, RBX_ECUDA, "creation of the slot events failed");
+        }
+    }
+    return RBX_OK;
 }
 
 rbx_status rbx_get_stats(rbx_job *j, int slot, rbx_stats *out)
@@ -840,7 +884,12 @@ rbx_status rbx_get_stats(rbx_job *j, int slot, rbx_stats *out)
     if (!j) return RBX_EINVAL;
     NEED(j, j->has_geom, RBX_ESTATE, "rbx_get_stats before rbx_set_geometry");
     NEED(j, slot >= 0 && slot < kHistSlots, RBX_EINVAL, "stats slot must be in [0, 64)");
-    return read_stats(j, slot, out, true, false);
+    if (!j->slot_ev) return read_stats(j, slot, out, true, false);
+    j->evp = j->slot_ev + (size_t)slot * EV_COUNT;
+    rbx_status st = read_stats(j, slot, out, true, true);
+    j->evp = j->ev;
+    if (out) out->n_launches = j->slot_launches[slot];
+    return st;
 }
 
 static double sweep_df(const double *freqs, int nf, int n)

@@ -86,6 +86,7 @@ _SIGS = {
     "rbx_set_linking": [_P, C.c_int],
     "rbx_update_set": [_P, C.POINTER(C.c_double), C.c_int, C.c_double, _P, C.POINTER(Stats)],
     "rbx_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "rbx_set_slot_timing": [_J, C.c_int],
     "rbx_selftest_bounded_wait": [C.POINTER(C.c_int)],
     "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
     "rbx_server_times": [_P, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -311,6 +312,10 @@ class Job:
 
     def update_frequency_async(self, f: float, df: float, data: torch.Tensor, slot: int = 0):
         self._check(self.L.rbx_update_frequency_async(self.h, f, df, _ptr(data), slot))
+
+    def set_slot_timing(self, on: bool = True):
+        """Per-slot device timings for update_frequency_async (rbx_set_slot_timing)."""
+        self._check(self.L.rbx_set_slot_timing(self.h, int(on)))
 
     def get_stats(self, slot: int = 0) -> dict:
         st = Stats()

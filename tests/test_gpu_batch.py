@@ -70,6 +70,33 @@ def test_async_stats_match_sync():
     j.close()
 
 
+def test_async_updates_with_slot_timing():
+    """Updates queued back to back with per-slot timing: each slot returns its update's
+    scalars (equal to the synchronous updates') and its own device timings and launch count."""
+    w = P.small_two_disc()
+    jobs, data = prepare([w], rbx.RBX_BF16)
+    j, d = jobs[0], data[0]
+    freqs = [float(f) for f in w.freqs]
+    sync = []
+    for f, dd in zip(freqs, d):
+        sync.append(j.update_frequency(f, 1e5, dd))
+    c_sync = j.get_model().cpu().numpy()
+    j.set_model(torch.tensor(w.c_init, dtype=torch.float32, device="cuda"))
+    j.set_slot_timing(True)
+    for s, (f, dd) in enumerate(zip(freqs, d)):
+        j.update_frequency_async(f, 1e5, dd, slot=s)
+    asy = [j.get_stats(s) for s in range(len(freqs))]
+    np.testing.assert_array_equal(j.get_model().cpu().numpy(), c_sync)
+    for a, b in zip(asy, sync):
+        for k in ("resid_norm2", "rms_dc", "max_abs_dc", "dm_norm", "n_uncovered"):
+            assert a[k] == b[k]
+        assert a["n_launches"] == b["n_launches"] > 0
+        assert a["ms_total"] > 0 and a["ms_kernel"]["trace"] > 0 and a["ms_kernel"]["gemm_bp"] > 0
+        assert a["ms_total"] >= a["ms_kernel"]["trace"]
+    j.set_slot_timing(False)
+    j.close()
+
+
 def test_batch_reports_a_failure_inside_the_sweep():
     """A non-finite datum at the second frequency fails that update (the model is kept) and the
     later updates succeed; the batch must still report the failure."""
