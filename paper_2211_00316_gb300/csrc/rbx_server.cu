@@ -7,9 +7,14 @@
 // sweep, and its sweep queued at once. Jobs on different streams overlap on the device.
 // Completed jobs are found by event query, their model and last-update scalars copied out,
 // their memory released (stream-ordered, no device-wide synchronisation), which admits the
-// next waiting requests. Latency is measured on the host from submission to completion.
+// next waiting requests. Latency is measured on the host from the moment rbx_server_submit is
+// entered to completion. The server's mutex guards only the queues and the published state
+// of each request: the worker takes a request off the queue under it, does the CUDA work
+// (job creation, uploads, completion, release) without it, and publishes the outcome under
+// it again, so a client's submit never waits behind device work.
 #include "rbx_internal.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -34,6 +39,7 @@ struct Request {
     std::vector<float> c0;
     std::vector<double> freqs;
     std::vector<unsigned char> data;   // nf x N x N complex64
+    // published state: read by clients, written under the server's mutex
     int state = RBX_REQ_QUEUED;
     rbx_status status = RBX_OK;
     std::string err;
@@ -42,7 +48,12 @@ struct Request {
     size_t bytes = 0;
     std::vector<float> c_out;
     rbx_stats last{};
-    // while running
+    // the worker's own while the request runs (never touched by clients)
+    rbx_status w_status = RBX_OK;
+    std::string w_err;
+    std::vector<float> w_c_out;
+    rbx_stats w_last{};
+    Clock::time_point w_done;
     rbx_job *job = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -81,15 +92,28 @@ static void release(Request &r)
     std::vector<unsigned char>().swap(r.data);
 }
 
+// Records a failure in the worker's private copy of the outcome (published by publish_end()).
 static void fail_req(Request &r, rbx_status st, const std::string &msg)
 {
-    r.status = st;
-    r.err = msg;
-    r.state = RBX_REQ_FAILED;
-    r.t_done = Clock::now();
+    r.w_status = st;
+    r.w_err = msg;
+    r.w_done = Clock::now();
 }
 
-// Create the job, upload model and data, queue the sweep and its completion event.
+// Copies the worker's outcome of an ended request into its published state. Called with
+// the server's mutex held.
+static void publish_end(Request &r)
+{
+    r.status = r.w_status;
+    r.err = r.w_err;
+    r.t_done = r.w_done;
+    r.last = r.w_last;
+    r.c_out.swap(r.w_c_out);
+    r.state = r.w_status == RBX_OK ? RBX_REQ_DONE : RBX_REQ_FAILED;
+}
+
+// Create the job, upload model and data, queue the sweep and its completion event. Runs
+// without the server's mutex; the request is already off the queue (state RUNNING).
 static bool start(Request &r)
 {
     auto cuda_fail = [&](const char *what, cudaError_t e) {
@@ -98,8 +122,6 @@ static bool start(Request &r)
         return false;
     };
     cudaError_t e;
-    r.t_start = Clock::now();
-    r.started = true;
     if ((e = cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail("stream", e);
     if ((e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail("event", e);
@@ -125,73 +147,98 @@ static bool start(Request &r)
         return false;
     }
     if ((e = cudaEventRecord(r.done, r.stream)) != cudaSuccess) return cuda_fail("completion event", e);
-    r.state = RBX_REQ_RUNNING;
     return true;
 }
 
+// Read the finished sweep's scalars and model (no mutex held).
 static void finish(Request &r)
 {
     rbx_stats st{};
     rbx_status s = job_read_sweep(r.job, (int)r.freqs.size(), &st);
     const size_t nxy = (size_t)r.g.nx * r.g.ny;
-    r.c_out.resize(nxy);
-    cudaError_t e = cudaMemcpyAsync(r.c_out.data(), job_model(r.job), nxy * sizeof(float), cudaMemcpyDeviceToHost,
+    r.w_c_out.resize(nxy);
+    cudaError_t e = cudaMemcpyAsync(r.w_c_out.data(), job_model(r.job), nxy * sizeof(float), cudaMemcpyDeviceToHost,
                                     r.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(r.stream);
-    r.t_done = Clock::now();
-    r.last = st;
+    r.w_done = Clock::now();
+    r.w_last = st;
     if (s != RBX_OK) {
         fail_req(r, s, rbx_last_error(r.job));
     } else if (e != cudaSuccess) {
         fail_req(r, RBX_ECUDA, std::string("model download: ") + cudaGetErrorString(e));
     } else {
-        r.state = RBX_REQ_DONE;
-        r.status = RBX_OK;
+        r.w_status = RBX_OK;
     }
 }
 
 static void worker_loop(rbx_server *s)
 {
     cudaSetDevice(s->device);
-    std::unique_lock<std::mutex> lk(s->mu);
+    // requests this worker runs; only the worker touches this list
+    std::vector<std::shared_ptr<Request>> running;
     while (true) {
         bool progressed = false;
-        // retire completed jobs
-        for (size_t k = 0; k < s->inflight.size();) {
-            Request &r = *s->reqs[s->inflight[k]];
+        // retire completed jobs: CUDA work unlocked, the outcome published under the mutex
+        for (size_t k = 0; k < running.size();) {
+            Request &r = *running[k];
             cudaError_t q = cudaEventQuery(r.done);
             if (q == cudaErrorNotReady) { ++k; continue; }
             if (q == cudaSuccess) finish(r);
             else fail_req(r, RBX_ECUDA, std::string("job failed: ") + cudaGetErrorString(q));
             release(r);
-            s->used -= r.bytes;
-            s->inflight.erase(s->inflight.begin() + k);
-            progressed = true;
-        }
-        // admit waiting requests in arrival order while they fit
-        while (!s->stop && !s->pending.empty() && (int)s->inflight.size() < s->max_inflight) {
-            Request &r = *s->reqs[s->pending.front()];
-            if (r.bytes > s->budget) {
-                fail_req(r, RBX_ENOMEM, "request needs more device memory than the server's budget");
-                s->pending.pop_front();
-                progressed = true;
-                continue;
-            }
-            if (s->used + r.bytes > s->budget) break;
-            s->pending.pop_front();
-            s->used += r.bytes;
-            if (start(r)) {
-                s->inflight.push_back(r.id);
-            } else {
-                release(r);
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                publish_end(r);
                 s->used -= r.bytes;
+                s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), r.id));
             }
+            running.erase(running.begin() + k);
             progressed = true;
         }
+        // admit waiting requests in arrival order while they fit: take one off the queue
+        // under the mutex, start it without the mutex
+        while (true) {
+            std::shared_ptr<Request> rp;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (s->stop || s->pending.empty() || (int)s->inflight.size() >= s->max_inflight) break;
+                Request &r = *s->reqs[s->pending.front()];
+                if (r.bytes > s->budget) {
+                    r.w_status = RBX_ENOMEM;
+                    r.w_err = "request needs more device memory than the server's budget";
+                    r.w_done = Clock::now();
+                    publish_end(r);
+                    s->pending.pop_front();
+                    progressed = true;
+                    s->cv.notify_all();
+                    continue;
+                }
+                if (s->used + r.bytes > s->budget) break;
+                s->pending.pop_front();
+                s->used += r.bytes;
+                s->inflight.push_back(r.id);
+                r.state = RBX_REQ_RUNNING;   // no longer cancellable; the worker owns its buffers
+                r.started = true;
+                r.t_start = Clock::now();
+                rp = s->reqs[r.id];
+            }
+            progressed = true;
+            if (start(*rp)) {
+                running.push_back(rp);
+            } else {
+                release(*rp);
+                std::lock_guard<std::mutex> lk(s->mu);
+                publish_end(*rp);
+                s->used -= rp->bytes;
+                s->inflight.erase(std::find(s->inflight.begin(), s->inflight.end(), rp->id));
+            }
+        }
+        std::unique_lock<std::mutex> lk(s->mu);
         if (progressed) s->cv.notify_all();
-        if (s->stop && s->inflight.empty()) break;
+        if (s->stop && running.empty()) break;
         s->cv.wait_for(lk, std::chrono::microseconds(progressed ? 0 : 200));
     }
+    std::lock_guard<std::mutex> lk(s->mu);
     for (long long id : s->pending) {
         Request &r = *s->reqs[id];
         r.state = RBX_REQ_CANCELLED;
@@ -235,9 +282,12 @@ rbx_status rbx_server_create(rbx_server **out, size_t hbm_budget_bytes, int max_
 rbx_status rbx_server_submit(rbx_server *s, const rbx_geometry *g, const float *c_init_host, const double *freqs_host,
                              int nf, const void *data_host, long long *ticket)
 {
+    // latency counts from here: the copies of the inputs below are part of it
+    const Clock::time_point t_call = Clock::now();
     if (!s || !g || !c_init_host || !freqs_host || !data_host || !ticket || nf < 1) return RBX_EINVAL;
     if (g->nx < 1 || g->ny < 1 || g->n_xducers < 1 || nf > kHistSlots) return RBX_EINVAL;
     auto r = std::make_shared<Request>();
+    r->t_submit = t_call;
     r->g = *g;
     const size_t nxy = (size_t)g->nx * g->ny, nn = (size_t)g->n_xducers * g->n_xducers;
     try {
@@ -252,7 +302,6 @@ rbx_status rbx_server_submit(rbx_server *s, const rbx_geometry *g, const float *
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return RBX_ESTATE;
     r->id = s->next_id++;
-    r->t_submit = Clock::now();
     s->reqs[r->id] = r;
     s->pending.push_back(r->id);
     *ticket = r->id;
