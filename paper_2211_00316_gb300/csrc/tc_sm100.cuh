@@ -1,7 +1,7 @@
 // Inline-PTX building blocks for the tensor-core contractions on sm_103a:
 // mbarriers, TMA tile loads, tensor-memory allocation, tcgen05.mma and tcgen05.ld.
-// Every wait is bounded (about a second of clock cycles) and reports a timeout instead
-// of spinning forever.
+// Every wait is bounded (one second of wall time, read from the global nanosecond timer)
+// and reports a timeout instead of spinning forever.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -10,7 +10,17 @@
 namespace rbx {
 namespace tc {
 
-constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+// Bound of every wait in nanoseconds of the global timer. Wall time, not SM cycles: the
+// epilogue warps of a CTA wait for its whole K loop, and a bound in cycles would stretch or
+// shrink with the SM clock.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -40,12 +50,13 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *b, uint32_t parity)
         : "memory");
     return ok;
 }
-// true when the phase with the given parity completed, false after ~1 s
+// true when the phase with the given parity completed, false after kWaitNs of wall time
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity)
 {
-    long long t0 = clock64();
+    if (mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(b, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
     return true;
 }
 
