@@ -193,10 +193,13 @@ rbx_status rbx_predict(rbx_job *job, double freq_hz, void *g_dev);
  *  without its scalar factor Delta omega m / ((2 pi)^3 omega)). */
 rbx_status rbx_adjoint(rbx_job *job, double freq_hz, const void *R_dev, void *out_dev, int preconditioned);
 
-/* One Hessian-free update at frequency f with sweep spacing df (Delta omega = 2 pi df):
- * trace (a1-a4), direct Green's function, Born prediction and residual against data_dev
- * (N x N complex64), preconditioned back-projection, m <- m + tau dm on the mask and
- * c = m^-1/2 (water outside the mask). Synchronises and fills *out (may be NULL). */
+/* One Hessian-free update at frequency f with sweep spacing df (Delta omega = 2 pi df),
+ * the update of Eqs. sound_speed_update / sound_speed_update2 with the step length of
+ * Sec. 3.4: trace (a1-a4), direct Green's function, Born prediction and residual against
+ * data_dev (N x N complex64, Eq. residual), preconditioned back-projection
+ * dm = -(Delta omega / (2 pi)^3) (m / omega) Re sum_{e,r} W_er u_e u_r R[e,r], then
+ * m <- m + tau dm on the mask and c = m^-1/2 (water outside the mask, Sec. 6.3).
+ * Synchronises and fills *out (may be NULL). */
 rbx_status rbx_update_frequency(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_dev, rbx_stats *out);
 
 /* Steps a5-a9 alone: one update on the job's current tables (from rbx_trace_rays or
@@ -252,7 +255,11 @@ rbx_status rbx_reconstruct(rbx_job *job, const double *freqs_hz, int nf, const v
  * (uint8), each [n_xducers][n_nodes] as in rbx_set_tables (a = 0: uncovered), and the Born
  * weights v_dev (n_nodes float32, v = omega^2 dA dm per mask node); D_dev is N x N complex64.
  * It allocates nothing: the split partial sums live in a fixed 8 MiB array inside the
- * library, so n_xducers must be <= 1024 (RBX_EINVAL otherwise). The first call on each
+ * library, so n_xducers must be <= 1024 (RBX_EINVAL otherwise). The contraction splits the
+ * mask nodes over at most floor(2^20 / N^2) CTAs per tile pair (the array holds that many
+ * N x N partial sums): at N = 1024 it runs unsplit, one CTA per upper 64 x 64 tile pair
+ * (136 CTAs), each looping over all nodes, so the largest sizes run well below the speed of
+ * rbx_forward. The first call on each
  * device looks up that array's device address (it may load the module): make it before any
  * stream capture. All calls share the array; calls that overlap on the GPU race and must be
  * serialised by the caller. Work is queued on cuda_stream (NULL: legacy default stream).
@@ -343,7 +350,7 @@ rbx_status rbx_get_tuning(const rbx_job *job, int *fwd_splits, int *candidates_t
 rbx_status rbx_pool_usage(size_t *used, size_t *reserved, int trim);
 
 /* Diagnostic of the failure handling (the paper has no counterpart). Every wait of the
- * tensor-core kernels on a barrier or a copy is bounded: after about one second of spinning
+ * tensor-core kernels on a barrier or a copy is bounded: after one second of wall time
  * the kernel records a timeout, stops and frees what it holds, and the call returns
  * RBX_ETIMEOUT. This runs one kernel on the current device whose single thread waits, with
  * that same bound, on a barrier that nothing ever signals. *timed_out = 1 when the wait gave
