@@ -176,15 +176,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, f: float) -> dict:
-    """The FP64 oracle, as it stands, on a bounded sample of one update of the workload,
-    scaled to freq-updates/s. Each part runs with all host threads busy: ray fans of
-    4 x threads transducers (tables), the Born forward over all mask nodes for the
-    (2 x threads)^2 (e, r) entries of 2 x threads fans, and the unfactorised back-projection
-    at 32 x threads mask nodes; the O(N^2) direct Green's function and the update are
-    negligible beside them."""
+def cpu_sample(w, f: float, o, tables_at) -> dict:
+    """A bounded sample of one update of the FP64 oracle, as it stands, scaled to a whole
+    update: ray fans of 4 x threads transducers (tables), the Born forward over all mask nodes
+    for the (2 x threads)^2 (e, r) entries of 2 x threads fans, and the unfactorised
+    back-projection at 32 x threads mask nodes on the workload's own tables (tables_at: the
+    oracle tables of all fans at those nodes); the O(N^2) direct Green's function and the
+    update are negligible beside them."""
     from oracle import oracle as O
-    o = O.Oracle(w.geom)
     N, X = o.N, o.X
     rng = np.random.default_rng(0)
     nth = O.Oracle.threads()
@@ -201,35 +200,114 @@ def cpu_baseline(w, f: float) -> dict:
     t0 = time.perf_counter()
     O.forward_rows(o, f, tb.T[:nr], tb.a[:nr], tb.K[:nr], v)
     t_fwd = (time.perf_counter() - t0) / (nr * nr) * N * N
-    nn = 32 * nth
-    Ts, As, Gs, Ks, Ds = (rng.uniform(1e-5, 1e-4, (N, nn)), rng.uniform(1, 10, (N, nn)),
-                          rng.uniform(-3, 3, (N, nn)), np.zeros((N, nn), np.int32), rng.uniform(0, 0.01, (N, nn)))
+    T, a, gam, K, dg = tables_at
+    nn = T.shape[1]
     R = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
     t0 = time.perf_counter()
-    O.backproject_nodes(o, f, Ts, As, Gs, Ks, Ds, R)
+    O.backproject_nodes(o, f, T, a, gam, K, dg, R)
     t_bp = (time.perf_counter() - t0) / nn * X
     total = t_fields + t_rays + t_fwd + t_bp
-    return {"value": 1.0 / total, "unit": UNIT, "cores": nth, "kind": "oracle",
+    return {"seconds_per_update": total, "cores": nth,
             "sample": (f"one update extrapolated from: ray fans of {nfans}/{N} transducers, Born forward of "
                        f"{nr}x{nr}/{N}x{N} (e,r) entries over all {X} mask nodes, back-projection at {nn}/{X} "
-                       f"nodes (s per full update: rays {t_rays:.1f}, forward {t_fwd:.1f}, "
-                       f"back-projection {t_bp:.1f})"),
-            "seconds_per_update": total}
+                       f"nodes on the workload's tables (s per full update: rays {t_rays:.1f}, forward {t_fwd:.1f}, "
+                       f"back-projection {t_bp:.1f})")}
+
+
+def oracle_tables_at(w, f: float, o, nodes):
+    """The oracle's tables of all fans at the given mask nodes (for the sampled back-projection)."""
+    ns, f6 = o.fields_for(w.c_init, f)
+    tb = o.tables(f6)
+    og = type(o)(w.geom)
+    og.X = len(nodes)
+    sub = [x[:, nodes] for x in (tb.T, tb.a, tb.gam, tb.K, tb.cov)]
+    dg = og.dgamma(sub[2].astype(np.float64), sub[4])
+    return sub[0], sub[1], sub[2], sub[3], dg
+
+
+def cpu_full_update(w, f: float, data) -> dict:
+    """One whole update (a1-a9) of the FP64 oracle, as it stands, timed on all host threads."""
+    from oracle import oracle as O
+    o = O.Oracle(w.geom)
+    t0 = time.perf_counter()
+    _, _, bad = o.update_frequency(f, w.dfreq, np.asarray(w.c_init, np.float64), np.asarray(data, np.complex128))
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": O.Oracle.threads(), "kind": "oracle",
+            "sample": (f"one whole update of the workload at {f/1e6:.2f} MHz (tables of all {o.N} fans, Born forward "
+                       f"of all pairs, unfactorised back-projection at all {o.X} mask nodes, update): {dt:.1f} s"),
+            "seconds_per_update": dt}
+
+
+def time_noalloc(job, rbx, torch, g, f: float, stream, reps: int = 5) -> dict:
+    """Device time (CUDA events on the job's stream) of rbx_forward and of
+    rbx_forward_noalloc on the job's own tables for one perturbation: 3 warm-up calls each,
+    then the mean of reps."""
+    import ctypes as C
+    L = rbx.load()
+    job.trace_rays(f)
+    t = job.get_tables()
+    T, a, K = t["T"], t["a"], t["K"]
+    del t
+    N, X = job.N, job.X
+    rng = np.random.default_rng(9)
+    dm = torch.tensor(rng.standard_normal((g.ny, g.nx)) * 1e-9, dtype=torch.float32, device="cuda")
+    idx = job.mask_idx().long()
+    w = 2 * math.pi * f
+    v = (dm.reshape(-1)[idx].double() * (w * w * g.dx ** 2)).float().contiguous()
+    D = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+    err = C.create_string_buffer(256)
+
+    def na():
+        st = L.rbx_forward_noalloc(T.data_ptr(), a.data_ptr(), K.data_ptr(), v.data_ptr(), N, X, f, g.c0,
+                                   D.data_ptr(), C.c_void_p(stream.cuda_stream), err, len(err))
+        assert st == 0, err.value.decode()
+
+    out = {}
+    for name, fn in (("rbx_forward", lambda: job.forward(f, dm)), ("rbx_forward_noalloc", na)):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+    out["scratch_split_cap"] = (1 << 20) // (N * N)    # 8 MiB of float2 partial sums / (N x N per split)
+    out["note"] = ("rbx_forward at the job's precision (synthesis pass + contraction); rbx_forward_noalloc FP32 SIMT "
+                   "with the Green's functions formed in the tile loads, unsplit at N = 1024")
+    return out
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import oracle as O
     w = workload(args.workload, 0)
-    vals = []
+    o = O.Oracle(w.geom)
     t_start = time.perf_counter()
-    for k in range(args.steps):
+    # the sampled back-projection runs on the workload's own tables (those of the lowest
+    # frequency's window; its cost does not depend on the values)
+    nodes = np.linspace(0, o.X - 1, 32 * O.Oracle.threads()).astype(np.int64)
+    tab = oracle_tables_at(w, float(w.freqs[0]), o, nodes)
+    vals = []
+    for k in range(args.warmup + args.steps):
         f = float(w.freqs[k % len(w.freqs)])
-        cb = cpu_baseline(w, f)
-        vals.append(cb["seconds_per_update"])
-    wall = time.perf_counter() - t_start
+        cb = cpu_sample(w, f, o, tab)
+        if k >= args.warmup:
+            vals.append(cb["seconds_per_update"])
     value = len(vals) / sum(vals)
+    # one whole update beside the sampled steps, on the oracle's own data (prediction on the
+    # true model + 40 dB noise)
+    full = None
+    if not args.no_cpu_baseline:
+        from paper_2211_00316_gb300 import phantoms as P
+        f0 = float(w.freqs[0])
+        clean, _ = o.predict(f0, w.c_true)
+        full = cpu_full_update(w, f0, P.add_noise(clean, w.snr_db, seed=100))
+    wall = time.perf_counter() - t_start
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
@@ -237,7 +315,7 @@ def run_reference(args):
             "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": value,
                              "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": wall}
+            "full_update": full, "wall_s": wall}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -260,12 +338,15 @@ def slice_pool(n_slices: int, rbx, P, torch) -> list:
     return pool
 
 
-def batched_form(args, rbx, P, torch) -> dict:
+def batched_form(args, rbx, P, torch, pool=None, steps=None, warmup=None, variants=None) -> dict:
     """32 independent slices of uneven size, each a full 10-frequency sweep (320 updates per
     step): one CUDA graph of all sweeps (BF16), the same work as plain multi-stream launches,
     and the plain per-job forms (each job's sweep after the other's, synchronising per update)
-    in BF16 and FP32."""
-    pool = slice_pool(args.slices, rbx, P, torch)
+    in BF16 and FP32. variants: the forms to time (default: all five)."""
+    pool = pool or slice_pool(args.slices, rbx, P, torch)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    variants = variants or ("graph_bf16", "streams_bf16", "sequential_bf16", "graph_fp32", "sequential_fp32")
     freqs = [w.freqs for w, _ in pool]
     updates = sum(len(f) for f in freqs)
     out = {"updates_per_step": updates}
@@ -286,11 +367,13 @@ def batched_form(args, rbx, P, torch) -> dict:
             j.set_model(torch.tensor(w.c_init, dtype=torch.float32, device="cuda"))
 
     def timed(name, jobs, run):
-        for _ in range(args.warmup):
+        if name not in variants:
+            return
+        for _ in range(warmup):
             reset(jobs)
             run()
         dev, wall = [], []
-        for _ in range(args.steps):
+        for _ in range(steps):
             reset(jobs)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -316,8 +399,7 @@ def batched_form(args, rbx, P, torch) -> dict:
         reset(jobs)
         batch_run = lambda g: (lambda: rbx.batch_run(jobs, freqs, data, use_graph=g)[1])
         timed(f"graph_{tag}", jobs, batch_run(True))
-        if tag == "bf16":
-            timed(f"streams_{tag}", jobs, batch_run(False))
+        timed(f"streams_{tag}", jobs, batch_run(False))
         timed(f"sequential_{tag}", jobs, sequential(jobs, data))
         out[f"device_bytes_{tag}"] = {"jobs_measured": int(used1 - used0 + data_bytes), "estimate": int(est)}
         for j in jobs:
@@ -327,6 +409,7 @@ def batched_form(args, rbx, P, torch) -> dict:
     # agreement of the BF16 graph form with the plain FP32 form after the whole sweep
     diffs = [float(np.sqrt(np.mean((a - b) ** 2))) for a, b in zip(models["graph_bf16"], models["sequential_fp32"])]
     same = all(np.array_equal(a, b) for a, b in zip(models["graph_bf16"], models["sequential_bf16"]))
+    out["graph_bf16_over_sequential_fp32"] = out["graph_bf16"]["value"] / out["sequential_fp32"]["value"]
     out["rms_dc_bf16_vs_fp32_m_s"] = {"max": max(diffs), "median": float(np.median(diffs))}
     # error against the true model on the mask after the sweep, per slice: initial, BF16, FP32
     errs = []
@@ -344,9 +427,11 @@ def batched_form(args, rbx, P, torch) -> dict:
 def served_form(rbx, P, torch, pool, n_req: int, rate: float, budget: float, max_inflight: int, closed: int,
                 serial_fp32: bool) -> dict:
     """Poisson arrivals (seeded) of reconstruction requests drawn from the slice pool, each a full
-    sweep, submitted to the library's server; latency = submission to completion (server clock).
-    Also a closed-loop burst (all requests at once: maximum throughput) and, optionally, the same
-    arrival stream served by the plain per-job FP32 form one request after the other."""
+    sweep, submitted to the library's server. Latency of both arms = scheduled arrival to
+    completion: for the served form, the server's submit-to-completion time plus the lag of the
+    submit call behind its scheduled arrival (host clock). Also a closed-loop burst (all
+    requests at once: maximum throughput) and, optionally, the same arrival stream served by the
+    plain per-job FP32 form one request after the other."""
     rng = np.random.default_rng(5)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     res = {"requests": n_req, "rate_req_s": rate, "hbm_budget_gb": budget / 1e9, "max_inflight": max_inflight}
@@ -360,19 +445,22 @@ def served_form(rbx, P, torch, pool, n_req: int, rate: float, budget: float, max
     for t in warm:
         assert srv.wait(t, 600.0) == 0
     t0 = time.perf_counter()
-    tickets = []
+    tickets, lag = [], []
     for k in range(n_req):
         dt = t0 + arrivals[k] - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
         w, d = pool[k % len(pool)]
+        lag.append(time.perf_counter() - (t0 + arrivals[k]))   # submit call behind its scheduled arrival
         tickets.append(srv.submit(w.geom, w.c_init, w.freqs, d))
     for t in tickets:
         assert srv.wait(t, 600.0) == 0, srv.poll(t)["error"]
     tm = [srv.times(t) for t in tickets]
     ups = sum(len(pool[k % len(pool)][0].freqs) for k in range(n_req))
     span = max(x["end"] for x in tm) - min(x["submit"] for x in tm)
-    res["open_loop"] = dict(pct([x["end"] - x["submit"] for x in tm]),
+    res["open_loop"] = dict(pct([x["end"] - x["submit"] + l for x, l in zip(tm, lag)]),
+                            from_submit=pct([x["end"] - x["submit"] for x in tm]),
+                            submit_lag_max_s=float(max(lag)),
                             queue_wait_p99_s=float(np.percentile([x["start"] - x["submit"] for x in tm], 99)),
                             updates_per_s=ups / span)
     if closed > 0:
@@ -471,8 +559,10 @@ def main():
                     help="frequencies per update (rbx_update_set); value then counts frequencies per second")
     ap.add_argument("--log-jsonl", default=None,
                     help="append one JSON line per timed update (frequency, residual, model change, stage times)")
-    ap.add_argument("--serve-requests", type=int, default=48,
-                    help="default workload: requests of the short served run reported beside throughput (0 = none)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="default workload: skip the batched and served forms reported beside throughput")
+    ap.add_argument("--forms-steps", type=int, default=3, help="batched form beside the default workload: timed steps")
+    ap.add_argument("--forms-warmup", type=int, default=3, help="batched form beside the default workload: warm-up")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -599,15 +689,25 @@ def main():
             e2e = {"value": REP.aggregate_throughput(world * args.steps, el), "unit": UNIT,
                    "h2d_bytes_per_step": N * N * 8,
                    "d2h_bytes_per_step": g.nx * g.ny * 4}
+        # the allocation-free Born forward (rbx_forward_noalloc: Green's functions formed inside an
+        # FP32 SIMT contraction, fixed scratch) beside rbx_forward on the same tables
+        noalloc = None
+        if not args.no_forms and world == 1 and N <= 1024:
+            noalloc = time_noalloc(job, rbx, torch, g, float(w.freqs[fidx[0]]), stream)
         job.close()
 
-    # request latency of the served form: a short seeded Poisson stream of uneven requests
-    serve = None
-    if args.serve_requests > 0:
+    # the batched and served forms on the uneven slices (one GPU): the batched graph against the
+    # plain per-job FP32 form, and the Poisson request stream with its serial FP32 replay
+    serve, batched = None, None
+    if not args.no_forms and world == 1:
         torch.cuda.empty_cache()
         pool = slice_pool(args.slices, rbx, P, torch)
-        serve = served_form(rbx, P, torch, pool, args.serve_requests, args.rate, args.budget_gb * 1e9,
-                            args.max_inflight, args.serve_requests, False)
+        batched = batched_form(args, rbx, P, torch, pool=pool, steps=args.forms_steps, warmup=args.forms_warmup,
+                               variants=("graph_bf16", "sequential_bf16", "sequential_fp32"))
+        torch.cuda.empty_cache()
+        if args.requests > 0:
+            serve = served_form(rbx, P, torch, pool, args.requests, args.rate, args.budget_gb * 1e9,
+                                args.max_inflight, args.closed, not args.no_serial)
         del pool
 
     if rank != 0:
@@ -662,14 +762,35 @@ def main():
                                            for k in ("ms_trace", "ms_forward", "ms_backproj", "ms_total")},
             "n_uncovered": int(stats[-1]["n_uncovered"]), "rms_dc_last": stats[-1]["rms_dc"],
             "relative_error_percent": re}
+    if noalloc is not None:
+        line["noalloc_forward"] = noalloc
+    if batched is not None:
+        line["forms"] = {
+            "workload": f"{args.slices} uneven slices (N in {{256,512,768,1024}}, grids 192-512 at 0.45-1.0 mm, "
+                        f"seeds 0-{args.slices - 1}), full 10-frequency sweeps, {batched['updates_per_step']} updates "
+                        f"per step, {args.forms_warmup} warm-up + {args.forms_steps} timed steps",
+            "graph_bf16": batched["graph_bf16"], "sequential_bf16": batched["sequential_bf16"],
+            "sequential_fp32": batched["sequential_fp32"],
+            "graph_bf16_over_sequential_fp32": batched["graph_bf16_over_sequential_fp32"],
+            "graph_equals_sequential_bf16": batched["graph_equals_sequential_bf16"],
+            "rms_dc_bf16_vs_fp32_m_s": batched["rms_dc_bf16_vs_fp32_m_s"],
+            "detail": batched}
     if serve is not None:
-        line["latency"] = {"p50_s": serve["open_loop"]["p50_s"], "p99_s": serve["open_loop"]["p99_s"],
+        ol = serve["open_loop"]
+        line["latency"] = {"p50_s": ol["p50_s"], "p99_s": ol["p99_s"], "from": "scheduled arrival",
                            "requests": serve["requests"], "rate_req_s": serve["rate_req_s"],
+                           "updates_per_s": ol["updates_per_s"],
                            "workload": f"Poisson arrivals of 10-frequency sweeps drawn from {args.slices} uneven "
                                        "slices (N 256-1024, grids 192-512), BF16, served form"}
+        if "serial_plain_fp32" in serve:
+            sp = serve["serial_plain_fp32"]
+            line["latency"]["serial_plain_fp32"] = {"p50_s": sp["p50_s"], "p99_s": sp["p99_s"],
+                                                    "updates_per_s_busy": sp["updates_per_s_busy"]}
+        if "closed_loop" in serve:
+            line["latency"]["closed_loop_updates_per_s"] = serve["closed_loop"]["updates_per_s"]
         line["serve"] = serve
     if not args.no_cpu_baseline and world == 1:
-        cb = cpu_baseline(w, float(w.freqs[0]))
+        cb = cpu_full_update(w, float(w.freqs[0]), noisy[uniq.index(0)])
         cb.pop("seconds_per_update", None)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
