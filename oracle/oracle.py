@@ -47,7 +47,7 @@ def lib():
 class OGeom(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("x0", C.c_double), ("y0", C.c_double),
                 ("N", C.c_int), ("R", C.c_double), ("mask_r", C.c_double), ("c0", C.c_double),
-                ("ds", C.c_double), ("weight_mode", C.c_int), ("tau", C.c_double)]
+                ("ds", C.c_double), ("weight_mode", C.c_int), ("tau", C.c_double), ("beta", C.POINTER(C.c_double))]
 
 
 class OMedium(C.Structure):
@@ -145,6 +145,12 @@ class Oracle:
         wm = geom.weight_mode if weight_mode is None else weight_mode
         self.g = OGeom(geom.nx, geom.ny, geom.dx, geom.x0, geom.y0, geom.n_xducers, geom.ring_radius,
                        geom.mask_radius, geom.c0, geom.ds, wm, geom.tau)
+        xy = getattr(geom, "xducer_xy", None)
+        if xy is not None:
+            # transducer positions on the ring (Sec. 2.1) as their angles, counterclockwise
+            xy = np.asarray(xy, np.float64).reshape(geom.n_xducers, 2)
+            self._beta = np.ascontiguousarray(np.arctan2(xy[:, 1], xy[:, 0]))
+            self.g.beta = _d(self._beta)
         self.L = lib()
         self.N = geom.n_xducers
         self.X = self.L.og_mask(C.byref(self.g), None)

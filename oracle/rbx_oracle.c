@@ -56,7 +56,12 @@ typedef struct {
     double R, mask_r, c0, ds;
     int weight_mode;        /* 0 literal scattering angle, 1 isochron */
     double tau;
+    const double *beta;     /* angle of transducer e on the ring, counterclockwise order (Sec. 2.1:
+                               the elements' positions); NULL: the uniform ring, beta_e = 2 pi e / N */
 } og_geom;
+
+/* Position angle beta_e of transducer e: x_e = R (cos beta_e, sin beta_e). */
+static double xducer_angle(const og_geom *g, int e) { return g->beta ? g->beta[e] : 2 * M_PI * e / g->N; }
 
 /* Medium seen by the ray tracer. mode 0: bilinear interpolation of six grid fields
  * (n, n_x, n_y, n_xx, n_xy, n_yy). mode 1: analytic linear velocity c = c1 + gx x + gy y,
@@ -426,9 +431,10 @@ static void raster_tri(const og_geom *g, const int *node2x, const vtx *A, const 
 static int max_steps(const og_geom *g) { return (int)ceil(3.0 * g->R / g->ds) + 8; }
 
 /* Ray fan of transducer e (a2): N-1 rays j = 1..N-1 leaving x_e at gamma0 = beta_e + pi/2
- * + pi j / N, i.e. at psi_j = -pi/2 + pi j / N from the inward normal, so that in water
- * ray j reaches receiver e + j (reading of the paper's ray linking for a full ring; the
- * fan replaces per-pair linking). Rays stop on the ring (radius R). Then (a3) the quad
+ * + pi j / N, i.e. at psi_j = -pi/2 + pi j / N from the inward normal, so that on the
+ * uniform ring ray j reaches receiver e + j in water (reading of the paper's ray linking for
+ * a full ring; the fan replaces per-pair linking). Other positions on the ring keep the same
+ * fan; the direct term then interpolates between the rays that bracket each receiver. Rays stop on the ring (radius R). Then (a3) the quad
  * between rays j, j+1 and samples i, i+1 (i >= 1) is split into triangles
  * (P[j,i], P[j+1,i], P[j+1,i+1]) and (P[j,i], P[j+1,i+1], P[j,i+1]) and rasterised.
  * exits[(j-1)*4 + {0,1,2,3}] = (exit angle, T, a, K) of ray j on the ring.
@@ -436,7 +442,7 @@ static int max_steps(const og_geom *g) { return (int)ceil(3.0 * g->R / g->ds) + 
 static int fan_tables(const og_geom *g, const og_medium *med, const int *node2x, int e, fan_out *o, double *exits)
 {
     int N = g->N, maxs = max_steps(g), bad = 0;
-    double be = 2 * M_PI * e / N, xe = g->R * cos(be), ye = g->R * sin(be);
+    double be = xducer_angle(g, e), xe = g->R * cos(be), ye = g->R * sin(be);
     osample *prev = malloc(sizeof(osample) * (maxs + 1)), *cur = malloc(sizeof(osample) * (maxs + 1));
     int Mprev = -1;
     for (int j = 1; j <= N - 1; j++) {
@@ -567,11 +573,11 @@ long og_direct_green(const og_geom *g, double f, const double *exits_all, double
 #pragma omp parallel for reduction(+ : clamped)
     for (int e = 0; e < N; e++) {
         const double *ex = exits_all + (size_t)e * (N - 1) * 4;
-        double be = 2 * M_PI * e / N;
+        double be = xducer_angle(g, e);
         for (int r = 0; r < N; r++) {
             double *o = out + 2 * ((size_t)e * N + r);
             if (r == e) { o[0] = o[1] = 0; continue; }
-            double t = wrap2pi(2 * M_PI * r / N - be);
+            double t = wrap2pi(xducer_angle(g, r) - be);
             int found = -1;
             double fr = 0;
             for (int j = 1; j <= N - 2; j++) {
@@ -623,12 +629,12 @@ long og_direct_green_linked(const og_geom *g, const og_medium *med, double f, co
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : clamped, unconv)
     for (int e = 0; e < N; e++) {
         const double *ex = exits_all + (size_t)e * (N - 1) * 4;
-        double be = 2 * M_PI * e / N, xe = g->R * cos(be), ye = g->R * sin(be);
+        double be = xducer_angle(g, e), xe = g->R * cos(be), ye = g->R * sin(be);
         osample *buf = malloc(sizeof(osample) * (maxs + 1));
         for (int r = 0; r < N; r++) {
             double *o = out + 2 * ((size_t)e * N + r);
             if (r == e) { o[0] = o[1] = 0; continue; }
-            double t = wrap2pi(2 * M_PI * r / N - be);
+            double t = wrap2pi(xducer_angle(g, r) - be);
             int found = -1;
             for (int j = 1; j <= N - 2; j++) {
                 double tj = wrap2pi(ex[(j - 1) * 4] - be), tk = wrap2pi(ex[j * 4] - be);

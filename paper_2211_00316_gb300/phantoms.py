@@ -24,7 +24,8 @@ class Geometry:
     """A centred square grid plus a ring of N point transducers (emitter and receiver each).
 
     Node (ix, iy) sits at (x0 + ix*dx, y0 + iy*dx); arrays are row-major [iy][ix].
-    Transducer e sits at R*(cos(2*pi*e/N), sin(2*pi*e/N)) (Sec. 2.1: elements on a ring).
+    Transducer e sits at R*(cos(2*pi*e/N), sin(2*pi*e/N)) (Sec. 2.1: elements on a ring), or
+    at xducer_xy[e] (N x 2, on the ring, counterclockwise) when that is given.
     """
     nx: int
     ny: int
@@ -36,6 +37,7 @@ class Geometry:
     ds_frac: float = 0.5            # ray step / grid spacing
     weight_mode: int = 0            # 0 literal scattering-angle weight, 1 isochron weight
     tau: float = 0.12               # step length (Sec. 6.3.2a); sweeps set step_length(df)
+    xducer_xy: np.ndarray | None = field(default=None, repr=False)   # N x 2 positions; None: uniform ring
 
     @property
     def x0(self) -> float:
@@ -100,6 +102,14 @@ def step_length(df: float) -> float:
 def _with_step(w: "Workload") -> "Workload":
     w.geom.tau = step_length(w.dfreq)
     return w
+
+
+def jittered_ring(n_xducers: int, ring_radius: float, jitter: float, seed: int) -> np.ndarray:
+    """N x 2 transducer positions on the ring, counterclockwise: element e at angle
+    2 pi (e + u_e) / N with u_e uniform in [-jitter, jitter] (jitter < 0.5 keeps the order)."""
+    rng = np.random.default_rng(seed)
+    th = 2 * math.pi * (np.arange(n_xducers) + rng.uniform(-jitter, jitter, n_xducers)) / n_xducers
+    return np.stack([ring_radius * np.cos(th), ring_radius * np.sin(th)], axis=1)
 
 
 def _disc(X, Y, cx, cy, r):

@@ -504,3 +504,80 @@ def test_amplitude_satisfies_transport_equation(oracle_mod):
         rel = np.abs(div) * s / np.hypot(Fx[1:-1, 1:-1], Fy[1:-1, 1:-1])
         sel = np.isfinite(rel) & (s > 15e-3)
         assert np.median(rel[sel]) < 0.01
+
+
+# --------------------------------------------------------------- transducers off the uniform ring
+
+
+def test_given_uniform_positions_reproduce_the_ring(oracle_mod):
+    """Positions passed explicitly (Sec. 2.1's x_e) at the uniform ring's angles give the
+    uniform ring's tables and direct Green's function (up to the rounding of the angles)."""
+    g = ring_geom(N=32, R=40e-3, nx=88)
+    th = 2 * np.pi * np.arange(32) / 32
+    gx = ring_geom(N=32, R=40e-3, nx=88, xducer_xy=np.stack([np.cos(th), np.sin(th)], 1) * 40e-3)
+    o, ox = oracle_mod.Oracle(g), oracle_mod.Oracle(gx)
+    c = np.full((g.ny, g.nx), C0)
+    c[30:50, 40:60] = 1530.0
+    out = []
+    for oo in (o, ox):
+        ns, f6 = oo.fields_for(c, 3e5)
+        tb = oo.tables(f6)
+        gd, cl = oo.direct_green(3e5, tb.exits)
+        out.append((tb, gd, cl))
+    (t0, g0_, c0_), (t1, g1, c1) = out
+    np.testing.assert_allclose(t1.T, t0.T, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(t1.a, t0.a, rtol=1e-9)
+    np.testing.assert_allclose(g1, g0_, rtol=1e-8, atol=1e-14)
+    # only receivers e +/- 1, exactly at the ends of the fan's exit range, may fall either side
+    assert c0_ <= 2 * 32 and c1 <= 2 * 32
+
+
+def test_jittered_ring_in_water_app_b(oracle_mod):
+    """Transducers at jittered angles on the ring (Sec. 2.1 allows any positions): in water the
+    tables still follow App. B within the ray-tube interpolation bound, and the direct Green's
+    function matches g0(|x_r - x_e|) within the error of linear interpolation in exit angle
+    between the bracketing rays, whose exits in water are spaced 2 pi / N apart: on an interval
+    of width h the interpolation error of a smooth f is at most h^2/8 max|f''|, here for
+    T(theta) = 2 R sin(theta/2) / c0 and a(theta) = (2 R sin(theta/2))^(-1/2). Receivers within
+    2 pi / N of the emitter lie outside the fan's exit range and are counted as clamped."""
+    N, R = 64, 45e-3
+    xy = P.jittered_ring(N, R, 0.3, seed=4)
+    g = ring_geom(N=N, R=R, xducer_xy=xy)
+    o = oracle_mod.Oracle(g)
+    ns, f6 = o.fields_for(np.full((g.ny, g.nx), C0), 3e5)
+    tb = o.tables(f6)
+    assert tb.uncovered == 0 and tb.bad_rays == 0
+    X, Y = g.coords()
+    nodes = np.stack([X.ravel()[o.idx], Y.ravel()[o.idx]], 1)
+    dpsi = math.pi / N
+    for e in range(0, N, 5):
+        s = np.linalg.norm(nodes - xy[e], axis=1)
+        assert np.all(np.abs(tb.T[e] - s / C0) <= s * dpsi ** 2 / 8 / C0 * 1.01 + 1e-15)
+        assert np.all(np.abs(tb.a[e] * np.sqrt(s) - 1) <= (3.0 / 32.0) * (g.ds / (s - g.ds)) ** 2 + dpsi ** 2 / 4)
+    f = 3e5
+    w = 2 * math.pi * f
+    gd, clamped = o.direct_green(f, tb.exits)
+    beta = np.arctan2(xy[:, 1], xy[:, 0])
+    h = 2 * math.pi / N
+    n_out = 0
+    for e in range(N):
+        for r in range(N):
+            if r == e:
+                assert gd[e, r] == 0
+                continue
+            t = (beta[r] - beta[e]) % (2 * math.pi)
+            if t < h or t > 2 * math.pi - h:
+                n_out += 1
+                continue
+            s = np.linalg.norm(xy[r] - xy[e])
+            # the bracketing interval [t0, t0 + h] and the curvature of T and a on it
+            t0 = h * math.floor(t / h)
+            tt = np.linspace(t0, t0 + h, 65)
+            dT = h * h / 8 * (R / (2 * C0)) * np.abs(np.sin(tt / 2)).max()
+            av = (2 * R * np.sin(tt / 2)) ** -0.5
+            d2a = np.abs(np.gradient(np.gradient(av, tt), tt)).max() * 1.05
+            da = h * h / 8 * d2a
+            Cg = (8 * math.pi * w / C0) ** -0.5
+            bound = Cg * (da + (2 * R * math.sin(t / 2)) ** -0.5 * w * dT) * 1.05 + 1e-12
+            assert abs(gd[e, r] - g0(f, s)) <= bound, (e, r, abs(gd[e, r] - g0(f, s)), bound)
+    assert clamped == n_out > 0
