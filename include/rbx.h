@@ -4,8 +4,9 @@
  *
  * Geometry (Sec. 2.1): a 2-D square grid of nx x ny nodes, node (ix, iy) at
  * (x0 + ix dx, y0 + iy dx), arrays row-major [iy][ix]; N point transducers on a ring of
- * radius R centred at the origin, transducer e at R (cos 2 pi e/N, sin 2 pi e/N), each
- * both emitter and receiver. The reconstruction mask is |x| <= mask_radius (Sec. 6.3).
+ * radius R centred at the origin, by default transducer e at R (cos 2 pi e/N, sin 2 pi e/N)
+ * (rbx_set_geometry also takes other positions on the ring), each both emitter and receiver.
+ * The reconstruction mask is |x| <= mask_radius (Sec. 6.3).
  *
  * Conventions shared by every call:
  *  - Pointers named *_dev are CUDA device pointers, *_host are host pointers. The caller
@@ -97,11 +98,20 @@ typedef struct {
  * without geometry. */
 rbx_status rbx_create(rbx_job **out, void *cuda_stream);
 
-/* Set the grid, ring and options (Sec. 2.1, Sec. 6.3) and allocate the job's device
- * workspaces (tables of N x X entries, X = mask nodes). Fails with RBX_EINVAL when the
- * grid does not contain the ring, mask_radius > ring_radius, N < 3, ds <= 0, or a ray
- * could need more than 2047 steps (2 R / ds). Resets the model to water (c0). */
-rbx_status rbx_set_geometry(rbx_job *job, const rbx_geometry *geom);
+/* Set the grid, ring, transducer positions and options (Sec. 2.1, Sec. 6.3) and allocate the
+ * job's device workspaces (tables of N x X entries, X = mask nodes). xducer_xy (host, 2N
+ * doubles x_0, y_0, x_1, ...; copied) places transducer e at (x_e, y_e); NULL places them
+ * uniformly, transducer e at R (cos 2 pi e/N, sin 2 pi e/N). Given positions must lie on the
+ * ring (| |x_e| - R | <= 1e-6 R; the angle atan2(y_e, x_e) is kept) and run counterclockwise
+ * around it once in index order, all distinct. Each transducer keeps the fan of N - 1 rays
+ * at pi j / N from the tangent (Sec. 4.4 reading): the direct term interpolates between the
+ * rays whose exits bracket each receiver, and receivers within about 2 pi / N of the emitter,
+ * outside the fan's exit range, take the nearest ray (counted in rbx_stats.n_clamped); the
+ * angular density is formed over the neighbouring indices e +/- 1.
+ * Fails with RBX_EINVAL when the grid does not contain the ring, mask_radius > ring_radius,
+ * N < 3, ds <= 0, a ray could need more than 2047 steps (2 R / ds), or the positions break
+ * the rules above. Resets the model to water (c0). */
+rbx_status rbx_set_geometry(rbx_job *job, const rbx_geometry *geom, const double *xducer_xy);
 
 /* Number of mask nodes X and their row-major node indices (idx_dev: X int32, may be NULL). */
 rbx_status rbx_mask(rbx_job *job, int *X_out, int *idx_dev);

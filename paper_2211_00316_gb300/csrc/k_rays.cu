@@ -70,6 +70,16 @@ __device__ __forceinline__ void field_eval(const float *__restrict__ F, const Ra
     }
 }
 
+// Whether a step from (x, y) reads only nodes of the uniform medium: the block map of the
+// current fields (k_uniform_nbhd); a null map says no.
+__device__ __forceinline__ bool uniform_at(const RayParams &p, float x, float y)
+{
+    if (!p.ublk) return false;
+    const int i = clampi_((int)floorf((x - p.x0) * p.inv_dx), 0, p.nx - 1) / kUBlock;
+    const int j = clampi_((int)floorf((y - p.y0) * p.inv_dx), 0, p.ny - 1) / kUBlock;
+    return __ldg(p.ublk + (size_t)j * p.nbx + i) != 0;
+}
+
 // A ray sample as a triangle vertex.
 struct Vtx {
     float x, y, T, a, kx, ky;
@@ -324,7 +334,7 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
     const float ds = p.ds, hds = 0.5f * p.ds, inv_dx = p.inv_dx, R2 = p.R * p.R;
     HitQueue hq{q_xi[wib], q_key[wib], q_v[wib], &q_cov[wib], 0};
 
-    const double be = 2.0 * 3.14159265358979323846 * e / N;
+    const double be = p.beta ? p.beta[e] : 2.0 * 3.14159265358979323846 * e / N;
     float x = (float)(p.R * cos(be)), y = (float)(p.R * sin(be));
     const float gam0 = (float)(be + 3.14159265358979323846 / 2 + 3.14159265358979323846 * j / N);
 
@@ -367,14 +377,32 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
     for (int i = 0; i < p.maxs; i++) {
         Vtx cur{};
         bool have = false;
-        if (alive && i < kin) {
-            // the step below in a uniform medium: straight, p constant, dx += ds dp / n
+        if (alive && (i < kin || uniform_at(p, x, y))) {
+            // the step below in a uniform medium (every node it reads holds the medium of the
+            // water, so F1 still holds its fields): straight, p constant, dx += ds dp / n; a
+            // chord that crosses the ring ends there as in the step below
             const float n = F1.n, in = rcp_nr(n);
             const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
-            kadd(x, cx, ds * tx); kadd(y, cy, ds * ty);
-            kadd(dxx, cdx, ds * (dpx * in)); kadd(dxy, cdy, ds * (dpy * in));
-            kadd(T, Tc, hds * (F1.nr + F1.nr));
-            if (LOSSY) kadd(B, Bc, hds * (F1.al + F1.al));
+            float inc = hds * (F1.nr + F1.nr), incB = LOSSY ? hds * (F1.al + F1.al) : 0.f;
+            const float xn = x + ds * tx, yn = y + ds * ty;
+            const bool last = xn * xn + yn * yn >= R2;
+            if (last) {
+                const float b = x * tx + y * ty, cc = i == 0 ? 0.f : x * x + y * y - R2;
+                const float disc = b * b - cc;
+                float t = -b + sqrtf(disc > 0.f ? disc : 0.f);
+                t = fminf(fmaxf(t, 0.f), ds);
+                const float fr = t / ds;
+                x = x + t * tx; y = y + t * ty;
+                inc *= fr;
+                incB *= fr;
+                dxx += fr * (ds * (dpx * in)); dxy += fr * (ds * (dpy * in));
+                field_eval<LOSSY, RAW>(F, p, x, y, F1);
+            } else {
+                kadd(x, cx, ds * tx); kadd(y, cy, ds * ty);
+                kadd(dxx, cdx, ds * (dpx * in)); kadd(dxy, cdy, ds * (dpy * in));
+            }
+            kadd(T, Tc, inc);
+            if (LOSSY) kadd(B, Bc, incB);
             const float J = dxx * ty - dxy * tx;
             if (i == 0) { sc1 = sqrtf(F1.nr * fabsf(J) / ds); Jlast = J; }
             else if (J * Jlast < 0.f) K++;
@@ -383,6 +411,11 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
             cur.a = sc1 * rsqrtf(F1.nr * fabsf(J));
             if (LOSSY) cur.a *= expf(-B);
             have = true;
+            if (last) {
+                alive = false;
+                if (lane < 31 || j == N - 1)
+                    exits[(size_t)e * (N - 1) + (j - 1)] = make_float4(atan2f(y, x), T, cur.a, (float)K);
+            }
         } else if (alive) {
             // stage 1 at x: normalise p to n(x), q_x = p/n, q_p = grad n
             const float n = F1.n, in = rcp_nr(n);
@@ -532,34 +565,74 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
     if (lane == 0 && *hq.cov) atomicAdd(&counters[0], (unsigned long long)*hq.cov);
 }
 
-// Largest radius of a node whose fields differ from the uniform medium of node (0, 0)
-// (n, alpha and the integrated slowness there, all derivatives zero); +inf when node (0, 0)
-// itself is not uniform.
-__global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsigned long long *ru)
+// Whether node k holds the uniform medium of node (0, 0) (n, alpha and the integrated
+// slowness equal to node (0, 0)'s, all derivatives zero); never when node (0, 0) itself has a
+// non-zero derivative.
+__device__ __forceinline__ bool node_uniform(const float4 *__restrict__ F, const RayParams &p, int k)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= p.nx * p.ny) return;
     const size_t nxy = (size_t)p.nx * p.ny;
     const float2 *F2 = reinterpret_cast<const float2 *>(F + nxy), *F3 = F2 + nxy;
     const float4 u0 = F[0], a0 = F[k];
     const float2 v0 = F2[0], v1 = F3[0], b0 = F2[k], b1 = F3[k];
-    const float4 u1 = make_float4(v0.x, v0.y, v1.x, v1.y), a1 = make_float4(b0.x, b0.y, b1.x, b1.y);
-    if (k == 0 && !(u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && u1.x == 0.f && u1.y == 0.f)) {
-        atomicMax(ru, (unsigned long long)__float_as_uint(__int_as_float(0x7f800000)));
-        return;
-    }
-    const bool uni = a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f &&
-                     a1.z == u1.z && a1.w == u1.w;
-    if (!uni) {
+    const bool flat0 = u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && v0.x == 0.f && v0.y == 0.f;
+    return flat0 && a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && b0.x == 0.f && b0.y == 0.f &&
+           b1.x == v1.x && b1.y == v1.y;
+}
+
+// Largest radius of a node whose fields differ from the uniform medium of node (0, 0); +inf
+// when node (0, 0) itself is not uniform.
+__global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsigned long long *ru)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.nx * p.ny) return;
+    if (!node_uniform(F, p, k)) {
         const float px = p.x0 + (float)(k % p.nx) * p.dx, py = p.y0 + (float)(k / p.nx) * p.dx;
-        atomicMax(ru, (unsigned long long)__float_as_uint(sqrtf(px * px + py * py)));
+        const float r = node_uniform(F, p, 0) ? sqrtf(px * px + py * py) : __int_as_float(0x7f800000);
+        atomicMax(ru, (unsigned long long)__float_as_uint(r));
     }
 }
 
-void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s)
+// bu[b] = 1 when every node of block b (kUBlock x kUBlock nodes, clipped at the grid's edge)
+// holds the uniform medium of node (0, 0).
+__global__ void k_uniform_blocks(const float4 *__restrict__ F, RayParams p, uint8_t *__restrict__ bu)
 {
-    const int n = p.nx * p.ny;
-    k_uniform_radius<<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float4 *>(fields), p, ru);
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nbx * p.nby) return;
+    const int bx = b % p.nbx, by = b / p.nbx;
+    bool u = true;
+    for (int dy = 0; dy < kUBlock; dy++)
+        for (int dx = 0; dx < kUBlock; dx++) {
+            const int ix = bx * kUBlock + dx, iy = by * kUBlock + dy;
+            if (ix < p.nx && iy < p.ny) u = u && node_uniform(F, p, iy * p.nx + ix);
+        }
+    bu[b] = u ? 1 : 0;
+}
+
+// ub[b] = 1 when the blocks within hb block widths of block b (those inside the grid) are all
+// uniform. hb covers a step's reach: a Heun step from a sample evaluates the fields at the
+// sample, at an auxiliary point and at the next sample, all within ds of it, and each bilinear
+// evaluation reads the four nodes of its cell, within sqrt(2) dx; so from any point of a block
+// with ub = 1 the step reads only uniform nodes and is the closed-form straight step.
+__global__ void k_uniform_nbhd(const uint8_t *__restrict__ bu, RayParams p, int hb, uint8_t *__restrict__ ub)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nbx * p.nby) return;
+    const int bx = b % p.nbx, by = b / p.nbx;
+    bool u = true;
+    for (int j = max(0, by - hb); j <= min(p.nby - 1, by + hb); j++)
+        for (int i = max(0, bx - hb); i <= min(p.nbx - 1, bx + hb); i++) u = u && bu[j * p.nbx + i];
+    ub[b] = u ? 1 : 0;
+}
+
+void launch_uniform_map(const float *fields, const RayParams &p, unsigned long long *ru, uint8_t *bu, uint8_t *ub,
+                        cudaStream_t s)
+{
+    const int n = p.nx * p.ny, nb = p.nbx * p.nby;
+    const float4 *F = reinterpret_cast<const float4 *>(fields);
+    k_uniform_radius<<<(n + 255) / 256, 256, 0, s>>>(F, p, ru);
+    k_uniform_blocks<<<(nb + 127) / 128, 128, 0, s>>>(F, p, bu);
+    const int hb = (int)ceil(((double)p.ds + 1.4142135623730951 * p.dx) / (kUBlock * (double)p.dx));
+    k_uniform_nbhd<<<(nb + 127) / 128, 128, 0, s>>>(bu, p, hb, ub);
 }
 
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
@@ -638,13 +711,6 @@ __device__ __forceinline__ float wrap2pi(float t)
     return t - TWO_PI * floorf(t / TWO_PI);
 }
 
-// Angle of receiver r relative to transducer e, in [0, 2 pi): (r - e) mod N ring steps of
-// step = 2 pi / N (no FP64 division or rounding to whole turns: FP64 is slow on this GPU).
-__device__ __forceinline__ double recv_rel(int r, int e, int N, double step)
-{
-    return (double)((r - e + N) % N) * step;
-}
-
 // An angle difference d in (-4 pi, 4 pi) taken to [0, 2 pi) by whole turns.
 __device__ __forceinline__ double wrap_turn(double d)
 {
@@ -656,48 +722,70 @@ __device__ __forceinline__ double wrap_turn(double d)
     return d;
 }
 
+// Angle of the receiver m ring places after transducer e (r = (e + m) mod N) relative to it,
+// in [0, 2 pi), increasing with m: m steps of step = 2 pi / N on the uniform ring (no FP64
+// division or rounding to whole turns: FP64 is slow on this GPU), else the difference of the
+// caller's position angles.
+__device__ __forceinline__ double recv_rel_m(int m, int e, int N, double step, const double *beta, double be)
+{
+    return beta ? wrap_turn(beta[(e + m) % N] - be) : (double)m * step;
+}
+
+// Position angle of transducer e.
+__device__ __forceinline__ double xducer_angle(int e, int N, double step, const double *beta)
+{
+    return beta ? beta[e] : (double)e * step;
+}
+
 // For every receiver r != e of fan e, the first pair of consecutive fan rays (j, j + 1),
 // j = 1..N-2, whose exit angles th (relative to beta_e, in [0, 2 pi)) bracket beta_r, as
-// first[r] = j, or INT_MAX when no pair does. Each pair marks the receivers between its two
-// exit angles (the bracket test on the candidates around them) and the smallest j wins, so a
-// fan costs O(N) rather than a scan over the pairs per receiver. Called by the whole block.
-__device__ void first_brackets(const float *th, int N, int e, double step, int *first)
+// first[r] = j, or INT_MAX when no pair does. relt[m] is the receiver angle relative to beta_e
+// of ring place m (increasing in m). Each pair marks the receivers between its two exit
+// angles (a binary search for the first, then the run up to the larger angle) and the
+// smallest j wins, so a fan costs O(N log N) rather than a scan over the pairs per receiver.
+// Called by the whole block.
+__device__ void first_brackets(const float *th, const float *relt, int N, int e, int *first)
 {
     for (int r = threadIdx.x; r < N; r += blockDim.x) first[r] = INT_MAX;
     __syncthreads();
-    const float scale = (float)N * 0.159154943091895f;   // receivers per radian
     for (int j = 1 + threadIdx.x; j <= N - 2; j += blockDim.x) {
         const float tj = th[j - 1], tk = th[j];
         if (tj == tk) continue;
         const float lo = fminf(tj, tk), hi = fmaxf(tj, tk);
-        const int m0 = max(1, (int)floorf(lo * scale) - 1), m1 = min(N - 1, (int)ceilf(hi * scale) + 1);
-        for (int m = m0; m <= m1; m++) {
-            const int r = (e + m) % N;
-            const float t = (float)((double)m * step);   // recv_rel(r, e, N, step)
-            if ((tj <= t && t <= tk) || (tk <= t && t <= tj)) atomicMin(&first[r], j);
+        int a = 1, b = N;   // first ring place m in [1, N - 1] with relt[m] >= lo (N: none)
+        while (a < b) {
+            const int c = (a + b) >> 1;
+            if (relt[c] < lo) a = c + 1; else b = c;
         }
+        for (int m = a; m <= N - 1 && relt[m] <= hi; m++) atomicMin(&first[(e + m) % N], j);
     }
     __syncthreads();
 }
 
-__global__ void k_direct_green(const float4 *__restrict__ exits, int N, float fhi, float flo, float C,
-                               float2 *__restrict__ g, unsigned long long *counters)
+__global__ void k_direct_green(const float4 *__restrict__ exits, int N, const double *__restrict__ beta, float fhi,
+                               float flo, float C, float2 *__restrict__ g, unsigned long long *counters)
 {
     extern __shared__ float4 ex[];
-    float *th = reinterpret_cast<float *>(ex + (N - 1));   // exit angle relative to beta_e, in [0, 2 pi)
-    int *first = reinterpret_cast<int *>(th + (N - 1));    // first bracketing pair per receiver
+    double *reld = reinterpret_cast<double *>(ex + (N - 1));   // receiver angle relative to beta_e by ring place
+    float *th = reinterpret_cast<float *>(reld + N);           // exit angle relative to beta_e, in [0, 2 pi)
+    float *relt = th + (N - 1);                                // reld rounded to float
+    int *first = reinterpret_cast<int *>(relt + N);            // first bracketing pair per receiver
     const int e = blockIdx.x;
-    const double step = 6.283185307179586476925 / N, be = (double)e * step;
+    const double step = 6.283185307179586476925 / N, be = xducer_angle(e, N, step, beta);
     for (int q = threadIdx.x; q < N - 1; q += blockDim.x) {
         float4 v = exits[(size_t)e * (N - 1) + q];
         ex[q] = v;
         th[q] = (float)wrap_turn((double)v.x - be);
     }
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        reld[m] = recv_rel_m(m, e, N, step, beta, be);
+        relt[m] = (float)reld[m];
+    }
     __syncthreads();
-    first_brackets(th, N, e, step, first);
+    first_brackets(th, relt, N, e, first);
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
         if (r == e) { g[(size_t)e * N + r] = make_float2(0.f, 0.f); continue; }
-        const double td = recv_rel(r, e, N, step);
+        const double td = reld[(r - e + N) % N];
         const float t = (float)td;
         // first consecutive pair (j, j+1) whose exit angles bracket beta_r
         const int found = first[r] == INT_MAX ? -1 : first[r];
@@ -728,14 +816,15 @@ __global__ void k_direct_green(const float4 *__restrict__ exits, int N, float fh
     }
 }
 
-void launch_direct_green(const float4 *exits, int N, double f, double c0, float2 *g, unsigned long long *counters,
-                         cudaStream_t s)
+void launch_direct_green(const float4 *exits, int N, const double *beta, double f, double c0, float2 *g,
+                         unsigned long long *counters, cudaStream_t s)
 {
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     float C = (float)(1.0 / sqrt(8.0 * 3.14159265358979323846 * (2.0 * 3.14159265358979323846 * f) / c0));
-    size_t smem = (size_t)(N - 1) * (sizeof(float4) + sizeof(float)) + (size_t)N * sizeof(int);   // <= 98 KB
+    size_t smem = (size_t)(N - 1) * (sizeof(float4) + sizeof(float)) +
+                  (size_t)N * (sizeof(double) + sizeof(float) + sizeof(int));   // <= 147 KB at N = 4095
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_direct_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_direct_green<<<N, 256, smem, s>>>(exits, N, fhi, flo, C, g, counters);
+    k_direct_green<<<N, 256, smem, s>>>(exits, N, beta, fhi, flo, C, g, counters);
 }
 
 // ---------------------------------------------------------------- ray linking
@@ -837,23 +926,26 @@ __device__ bool trace_one(const float *__restrict__ F, const RayParams &p, float
 // Linking, step 1, one block per transducer: the first bracketing pair of fan rays of every
 // receiver (as in k_direct_green), or the nearest fan ray where none brackets it, kept in the
 // unused first slot of linked[e][r] as j (> 0) or -j; the diagonal is zeroed.
-__global__ void k_link_brackets(const float4 *__restrict__ exits, int N, float4 *__restrict__ linked)
+__global__ void k_link_brackets(const float4 *__restrict__ exits, int N, const double *__restrict__ beta,
+                                float4 *__restrict__ linked)
 {
     extern __shared__ float4 ex_s[];
     float *th = reinterpret_cast<float *>(ex_s);
-    int *first = reinterpret_cast<int *>(th + (N - 1));
+    float *relt = th + (N - 1);
+    int *first = reinterpret_cast<int *>(relt + N);
     const int e = blockIdx.x;
-    const double step = 6.283185307179586476925 / N, be = (double)e * step;
+    const double step = 6.283185307179586476925 / N, be = xducer_angle(e, N, step, beta);
     for (int q = threadIdx.x; q < N - 1; q += blockDim.x)
         th[q] = (float)wrap_turn((double)exits[(size_t)e * (N - 1) + q].x - be);
+    for (int m = threadIdx.x; m < N; m += blockDim.x) relt[m] = (float)recv_rel_m(m, e, N, step, beta, be);
     __syncthreads();
-    first_brackets(th, N, e, step, first);
+    first_brackets(th, relt, N, e, first);
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (r != e) {
             int code = first[r];
             if (code == INT_MAX) {
-                const float t = (float)recv_rel(r, e, N, step);
+                const float t = relt[(r - e + N) % N];
                 int best = 1;
                 float bd = 1e30f;
                 for (int j = 1; j <= N - 1; j++) {
@@ -887,8 +979,8 @@ __global__ __launch_bounds__(128, 4) void k_link_rays(const float *__restrict__ 
     if (e >= N || m > N - 1) return;
     const int r = (e + m) % N;
     const double PI = 3.14159265358979323846, TWO_PI = 2.0 * PI;
-    const double step = TWO_PI / N, be = (double)e * step;
-    const double td = (double)m * step;   // recv_rel(r, e, N, step)
+    const double step = TWO_PI / N, be = xducer_angle(e, N, step, p.beta);
+    const double td = recv_rel_m(m, e, N, step, p.beta, be);
     float4 *slot = linked + (size_t)e * N + r;
     const int code = __float_as_int(slot->x);
     const float4 *ex = exits + (size_t)e * (N - 1);
@@ -961,8 +1053,9 @@ void launch_green_linked(const float4 *linked, int N, double f, double c0, float
 void launch_link_rays(const float *fields, const RayParams &p, const float4 *exits, int maxit, float4 *linked,
                       unsigned long long *counters, bool lossy, bool raw, cudaStream_t s)
 {
-    const size_t smem = (size_t)(p.N - 1) * sizeof(float) + (size_t)p.N * sizeof(int);   // <= 33 KB
-    k_link_brackets<<<p.N, 256, smem, s>>>(exits, p.N, linked);
+    const size_t smem = (size_t)(p.N - 1) * sizeof(float) + (size_t)p.N * (sizeof(float) + sizeof(int));   // <= 49 KB
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_link_brackets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_link_brackets<<<p.N, 256, smem, s>>>(exits, p.N, p.beta, linked);
     const double tol = 1e-6;
     const dim3 grd((p.N - 1 + 31) / 32, (p.N + 3) / 4);
     if (lossy && raw)

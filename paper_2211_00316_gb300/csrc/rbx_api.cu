@@ -94,7 +94,7 @@ static void free_ws(Workspace &w, cudaStream_t s)
 {
     void *ps[] = {w.hist, w.node2x, w.idx, w.rows, w.c, w.ns, w.tmp, w.fields, w.ns64, w.tmp64, w.tab, w.dg, w.exits, w.G, w.U,
                   w.kap, w.v, w.gdir, w.D, w.R, w.Rs, w.part, w.gpart, w.data, w.red, w.counters, w.alpha0, w.as64,
-                  w.dmacc, w.linked};
+                  w.dmacc, w.linked, w.beta, w.ublk, w.ublk0};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, s);
     tc_free(w.tc, s);
@@ -177,7 +177,7 @@ rbx_status rbx_synchronize(rbx_job *j)
     return RBX_OK;
 }
 
-rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
+rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom, const double *xducer_xy)
 {
     if (!j || !geom) return RBX_EINVAL;
     const rbx_geometry &g = *geom;
@@ -197,6 +197,27 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
          RBX_EINVAL, "the grid must contain the ring with one node to spare");
     NEED(j, max_steps(g) <= kMaxSteps, RBX_EINVAL, "ring_radius / ds too large (rays limited to 2047 steps)");
     NEED(j, (double)g.nx * g.ny < 2e9, RBX_EINVAL, "grid too large");
+    // caller-placed transducers (Sec. 2.1): on the ring, counterclockwise, once around
+    std::vector<double> beta;
+    if (xducer_xy) {
+        const double TWO_PI = 6.283185307179586476925;
+        beta.resize(g.n_xducers);
+        for (int e = 0; e < g.n_xducers; e++) {
+            const double x = xducer_xy[2 * e], y = xducer_xy[2 * e + 1];
+            NEED(j, std::isfinite(x) && std::isfinite(y) && std::fabs(std::hypot(x, y) - g.ring_radius) <= 1e-6 * g.ring_radius,
+                 RBX_EINVAL, "transducer positions must lie on the ring (|x_e| = ring_radius within 1e-6 relative)");
+            beta[e] = std::atan2(y, x);
+        }
+        double turn = 0.0;
+        for (int e = 0; e < g.n_xducers; e++) {
+            double d = beta[(e + 1) % g.n_xducers] - beta[e];
+            d -= TWO_PI * std::floor(d / TWO_PI);
+            NEED(j, d > 0.0, RBX_EINVAL, "transducer positions must be distinct");
+            turn += d;
+        }
+        NEED(j, std::fabs(turn - TWO_PI) <= 1e-9, RBX_EINVAL,
+             "transducer positions must run counterclockwise around the ring once, in index order");
+    }
 
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     free_ws(j->w, j->stream);
@@ -267,6 +288,15 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom)
     ALLOC(w.red, (size_t)residual_blocks(w.N) + 8 + 3 * (size_t)update_blocks(g.nx, g.ny) + 8);
     ALLOC(w.counters, 8);
     ALLOC(w.hist, (size_t)kHistSlots * kHistStride);
+    {
+        const size_t nb = (size_t)((g.nx + kUBlock - 1) / kUBlock) * ((g.ny + kUBlock - 1) / kUBlock);
+        ALLOC(w.ublk, nb);
+        ALLOC(w.ublk0, nb);
+    }
+    if (!beta.empty()) {
+        ALLOC(w.beta, N);
+        CUDA_TRY(j, cudaMemcpyAsync(w.beta, beta.data(), N * sizeof(double), cudaMemcpyHostToDevice, j->stream));
+    }
 #undef ALLOC
     launch_mask_idx(w.node2x, (int)nxy, w.idx, j->stream);
     launch_mask_rows(w.node2x, g.nx, g.ny, w.rows, j->stream);
@@ -382,6 +412,10 @@ static RayParams ray_params(const rbx_job *j)
     p.R = (float)j->g.ring_radius; p.ds = (float)j->g.ds; p.inv_dx = (float)(1.0 / j->g.dx);
     p.rmask = (float)j->g.mask_radius;
     p.maxs = max_steps(j->g);
+    p.beta = w.beta;
+    p.ublk = w.ublk;
+    p.nbx = (w.nx + kUBlock - 1) / kUBlock;
+    p.nby = (w.ny + kUBlock - 1) / kUBlock;
     return p;
 }
 
@@ -400,7 +434,7 @@ static rbx_status direct_green(rbx_job *j, double f, float2 *out)
         }
         launch_green_linked(w.linked, w.N, f, j->g.c0, out, j->stream);
     } else {
-        launch_direct_green(w.exits, w.N, f, j->g.c0, out, w.counters, j->stream);
+        launch_direct_green(w.exits, w.N, w.beta, f, j->g.c0, out, w.counters, j->stream);
     }
     LAUNCHED(j, 1);
     return RBX_OK;
@@ -433,10 +467,10 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
     const RayParams p = ray_params(j);
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
-    launch_uniform_radius(w.fields, p, w.counters + 7, j->stream);
+    launch_uniform_map(w.fields, p, w.counters + 7, w.ublk0, w.ublk, j->stream);
     launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->lossy, j->raw, j->stream);
     j->linked_valid = j->dg_valid = false;
-    LAUNCHED(j, 2);
+    LAUNCHED(j, 4);
     if ((st = record(j, EV_TRACE))) return st;
     if (j->g.precision == RBX_FP32 && (st = ensure_dgamma(j))) return st;
     if ((st = record(j, EV_TABLES))) return st;

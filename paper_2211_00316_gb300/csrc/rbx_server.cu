@@ -126,7 +126,7 @@ static bool start(Request &r)
         return cuda_fail("stream", e);
     if ((e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail("event", e);
     rbx_status st = rbx_create(&r.job, r.stream);
-    if (st == RBX_OK) st = rbx_set_geometry(r.job, &r.g);
+    if (st == RBX_OK) st = rbx_set_geometry(r.job, &r.g, nullptr);
     if (st != RBX_OK) {
         fail_req(r, st, r.job ? rbx_last_error(r.job) : "job creation failed");
         return false;

@@ -54,7 +54,7 @@ _P = C.c_void_p
 _J = C.c_void_p
 _SIGS = {
     "rbx_create": [C.POINTER(C.c_void_p), _P],
-    "rbx_set_geometry": [_J, C.POINTER(Geometry)],
+    "rbx_set_geometry": [_J, C.POINTER(Geometry), _P],
     "rbx_mask": [_J, C.POINTER(C.c_int), _P],
     "rbx_set_model": [_J, _P],
     "rbx_get_model": [_J, _P],
@@ -200,10 +200,13 @@ class Job:
 
     # ---------------------------------------------------------------- set-up
     def set_geometry(self, g, precision: int = RBX_FP32, weight_mode: int | None = None, tau: float | None = None):
-        """g: a phantoms.Geometry (or any object with the same attributes)."""
+        """g: a phantoms.Geometry (or any object with the same attributes); its xducer_xy
+        (N x 2, optional) places the transducers on the ring."""
         G = Geometry(g.nx, g.ny, g.dx, g.x0, g.y0, g.n_xducers, g.ring_radius, g.mask_radius, g.c0, g.ds,
                      g.weight_mode if weight_mode is None else weight_mode, g.tau if tau is None else tau, precision)
-        self._check(self.L.rbx_set_geometry(self.h, C.byref(G)))
+        xy = getattr(g, "xducer_xy", None)
+        xy = None if xy is None else np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1))
+        self._check(self.L.rbx_set_geometry(self.h, C.byref(G), None if xy is None else xy.ctypes.data))
         self.geom = g
         self.N, self.nx, self.ny = g.n_xducers, g.nx, g.ny
         X = C.c_int()
