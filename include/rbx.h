@@ -340,18 +340,33 @@ rbx_status rbx_server_destroy(rbx_server *srv);
 const char *rbx_last_error(const rbx_job *job);
 
 /* Autotuning of the BF16 forward contraction's K split (split across CTAs of each upper
- * tile pair, partial sums reduced in a fixed order). mode 1 (default): the first job of a
- * given (device, N, mask size, precision) in the process times up to five split counts on
- * its own operand planes inside rbx_set_geometry and keeps the fastest; later jobs of that
- * shape reuse it, so results within a process are reproducible. mode 0: the fixed
+ * tile pair, partial sums reduced in a fixed order) and, on the plain BF16 path, of its
+ * operand synthesis (separate pass or fused, see rbx_get_tuning_times). mode 1 (default): the
+ * first job of a given (device, N, mask size, precision) in the process times up to five
+ * split counts on its own operand planes inside rbx_set_geometry and keeps the fastest, then
+ * the two syntheses at that split; later jobs of that shape reuse the choice, so results
+ * within a process are reproducible. mode 0: the fixed
  * heuristic (about one CTA per SM), reproducible across processes. Other values only
- * query. Returns the previous mode. The choice changes the forward's summation order, so
- * results differ between split counts by rounding (within the BF16 tolerance). */
+ * query. Mode 2: the heuristic split with the fused-synthesis forward (see
+ * rbx_get_tuning_times). Returns the previous mode. The choice changes the forward's
+ * summation order, so results differ between split counts by rounding (within the BF16
+ * tolerance). */
 int rbx_autotune(int mode);
 
 /* The forward K split the job uses and the number of candidates it timed (0: reused or
  * heuristic). */
 rbx_status rbx_get_tuning(const rbx_job *job, int *fwd_splits, int *candidates_timed);
+
+/* Diagnostic of the tuner's second choice on the plain BF16 path (the paper has no
+ * counterpart): whether the Born forward forms its tensor-core operands from the tables inside
+ * the contraction (fused synthesis of the Green's functions, Eq. 2D_greens) instead of reading
+ * BF16 planes written by a separate synthesis pass. The tuner times, at the job's shape, the
+ * separate pass over both contractions' operands plus the forward GEMM against the
+ * back-projection's synthesis alone plus the fused forward, and keeps the faster. ms (4 floats,
+ * nullable) receives those times in that order (0 where not timed); *fused (nullable) = 1 when
+ * the job uses the fused forward. rbx_autotune(2) makes later jobs take the fused forward
+ * without timing (heuristic split, plain BF16 only). */
+rbx_status rbx_get_tuning_times(const rbx_job *job, float *ms, int *fused);
 
 /* Device memory of the stream-ordered pool all jobs of the current device allocate from:
  * bytes held by live allocations (used) and bytes the pool has taken from the device

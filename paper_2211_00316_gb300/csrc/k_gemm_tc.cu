@@ -49,6 +49,11 @@ __device__ __forceinline__ float phase_cycles_tc(float T, int K, float fhi, floa
     return r + 0.125f - 0.25f * (float)K;
 }
 
+// G v with its rounding fixed (no contraction left to the compiler), so every kernel that
+// forms the forward operands gives the same bits
+__device__ __forceinline__ float gv_re(float gr, float gi, float2 v) { return __fmaf_rn(gr, v.x, -__fmul_rn(gi, v.y)); }
+__device__ __forceinline__ float gv_im(float gr, float gi, float2 v) { return __fmaf_rn(gr, v.y, __fmul_rn(gi, v.x)); }
+
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
@@ -191,6 +196,163 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc(const __grid_constant__ M
             }
             fence_before();
             mbar_arrive(acce + buf);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// Fused-synthesis candidate of the plain BF16 forward (the tuner times it against the
+// separate synthesis pass plus k_forward_tc and keeps the faster): no operand planes. The
+// four epilogue warps, idle during the K loop of the plain forward (one accumulation
+// segment), form each stage's tiles from the tables themselves: G_e[x] for the 128 emitter
+// rows of the tile pair and G_r[x] v[x] for its 128 receiver rows (Eqs. 2D_greens, perturb1),
+// with the same phase, sine/cosine and rounding to BF16 as the synthesis pass, so D is the same
+// bit for bit. They store the values in the 128-byte-swizzled K-major layout the MMA
+// descriptors read (row r at 128 r bytes, its 16-byte chunk c at chunk c ^ (r mod 8)), make the
+// generic-proxy writes visible to the tensor cores' async proxy, and arrive on the stage's
+// barrier. Each table entry is formed once per tile pair it belongs to (N / 128 times), where
+// the separate pass forms it once and TMA streams the BF16 planes.
+__global__ __launch_bounds__(192, 1) void k_forward_tc_fused(const TabEntry *__restrict__ tab,
+                                                             const float2 *__restrict__ v, int N, int X, int ntile,
+                                                             int nk, int kper, float fhi, float flo, float C,
+                                                             float2 *__restrict__ part, unsigned *__restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = align1024(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + (size_t)F_STAGES * F_TILES * TILE);
+    uint64_t *empty = full + F_STAGES;
+    uint64_t *accf = empty + F_STAGES;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accf + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    int b = blockIdx.x, te = 0;
+    while (b >= ntile - te) { b -= ntile - te; te++; }
+    const int tr = te + b;
+    const int split = blockIdx.y;
+    const int c0 = split * kper, nc = min(nk, c0 + kper) - c0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < F_STAGES; s++) { mbar_init(full + s, 128); mbar_init(empty + s, 1); }
+        mbar_init(accf, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t ip = idesc_bf16(BM, BN, 0), in = idesc_bf16(BM, BN, 1);
+            const uint32_t dre = tmem, dim = tmem + BN;
+            bool ok = true;
+            for (int c = 0; c < nc && ok; c++) {
+                const int s = c % F_STAGES;
+                if (!mbar_wait(full + s, (c / F_STAGES) & 1)) { atomicOr(err, 2u); ok = false; break; }
+                fence_after();
+                const uint32_t base = smem_u32(tiles + (size_t)s * F_TILES * TILE);
+#pragma unroll
+                for (int k = 0; k < BK / 16; k++) {
+                    uint64_t a0 = desc_sw128(base + k * 32), a1 = desc_sw128(base + TILE + k * 32);
+                    uint64_t b0 = desc_sw128(base + 2 * TILE + k * 32), b1 = desc_sw128(base + 3 * TILE + k * 32);
+                    uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+                    mma_bf16(dre, a0, b0, ip, acc);
+                    mma_bf16(dre, a1, b1, in, 1u);
+                    mma_bf16(dim, a0, b1, ip, acc);
+                    mma_bf16(dim, a1, b0, ip, 1u);
+                }
+                mma_commit(empty + s);
+            }
+            if (nc > 0) mma_commit(accf);
+            if (nc > 0 && !mbar_wait(accf, 0)) atomicOr(err, 8u);
+        }
+        __syncwarp();
+    } else if (warp >= 2) {
+        // producers: warp w forms tile rows 32 (w - 2) .. +31 of both operands
+        const int pw = warp - 2;
+        bool ok = true;
+        for (int c = 0; c < nc && ok; c++) {
+            const int s = c % F_STAGES;
+            if (c >= F_STAGES) {
+                ok = __all_sync(0xffffffffu, mbar_wait(empty + s, ((c / F_STAGES) - 1) & 1));
+                if (!ok) {
+                    if (lane == 0) atomicOr(err, 1u);
+                    break;
+                }
+            }
+            uint8_t *base = tiles + (size_t)s * F_TILES * TILE;
+            const int kx = (c0 + c) * BK;
+            float2 vv[2];
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                const int x = kx + lane + 32 * q;
+                vv[q] = x < X ? v[x] : make_float2(0.f, 0.f);
+            }
+#pragma unroll 1
+            for (int rr = 0; rr < 32; rr++) {
+                const int r = pw * 32 + rr;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int row = (h ? tr : te) * BM + r;
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int col = lane + 32 * q, x = kx + col;
+                        float gr = 0.f, gi = 0.f;
+                        if (row < N && x < X) {
+                            const TabEntry t = tab[(size_t)row * X + x];
+                            if (t.idk != kUncovered) {
+                                float sn, cs;
+                                sincospif(2.f * phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &sn, &cs);
+                                gr = C * t.a * cs;
+                                gi = C * t.a * sn;
+                            }
+                        }
+                        const float re = h ? gv_re(gr, gi, vv[q]) : gr, im = h ? gv_im(gr, gi, vv[q]) : gi;
+                        const uint32_t off = (uint32_t)r * 128u + ((((uint32_t)col >> 3) ^ ((uint32_t)r & 7u)) << 4) +
+                                             (((uint32_t)col & 7u) << 1);
+                        *reinterpret_cast<__nv_bfloat16 *>(base + (2 * h) * TILE + off) = __float2bfloat16_rn(re);
+                        *reinterpret_cast<__nv_bfloat16 *>(base + (2 * h + 1) * TILE + off) = __float2bfloat16_rn(im);
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(full + s);
+        }
+        // epilogue: the single accumulation segment into the CTA's partial tile
+        const int sub = warp & 3, row = sub * 32 + lane;
+        const int e = te * BM + row;
+        float2 *P = part + (size_t)split * N * N + (size_t)e * N;
+        const uint32_t lanes = (uint32_t)(sub * 32) << 16;
+        if (ok && nc > 0) {
+            ok = __all_sync(0xffffffffu, mbar_wait(accf, 0));
+            fence_after();
+            if (!ok && lane == 0) atomicOr(err, 16u);
+        }
+        if (ok) {
+#pragma unroll 1
+            for (int cc = 0; cc < BN; cc += 32) {
+                float vr[32], vi[32];
+                if (nc > 0) {
+                    tmem_ld32(tmem + lanes + cc, vr);
+                    tmem_ld32(tmem + lanes + BN + cc, vi);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; i++) vr[i] = vi[i] = 0.f;
+                }
+                if (e < N) {
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const int r = tr * BN + cc + i;
+                        if (r < N) P[r] = make_float2(vr[i], vi[i]);
+                    }
+                }
+            }
         }
     }
     fence_before();
@@ -390,10 +552,6 @@ __device__ __forceinline__ void put_split(__nv_bfloat16 *hi, __nv_bfloat16 *lo, 
     if (lo) *lo = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// G v with its rounding fixed (no contraction left to the compiler), so both kernels that
-// write the forward planes give the same bits
-__device__ __forceinline__ float gv_re(float gr, float gi, float2 v) { return __fmaf_rn(gr, v.x, -__fmul_rn(gi, v.y)); }
-__device__ __forceinline__ float gv_im(float gr, float gi, float2 v) { return __fmaf_rn(gr, v.y, __fmul_rn(gi, v.x)); }
 
 // planes [4][Npad][Xpad]: Gre, Gim, (G v)re, (G v)im (then 4 lo planes when split);
 // G_e[x] = C a exp(i 2 pi (f T - K/4 + 1/8))
@@ -649,6 +807,8 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t st)
     }
     if (!ok) return false;
     ok = cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM) == cudaSuccess &&
+         cudaFuncSetAttribute(k_forward_tc_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM) ==
+             cudaSuccess &&
          cudaFuncSetAttribute(k_backproject_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM) ==
              cudaSuccess &&
          cudaFuncSetAttribute(k_backproject_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM) ==
@@ -661,7 +821,12 @@ bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t st)
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, bool>, int> g_tune;   // (device, N, X, split) -> K chunks per CTA
+struct TuneChoice {
+    int kper = 1;
+    bool fused = false;
+    float ms[4] = {0.f, 0.f, 0.f, 0.f};
+};
+std::map<std::tuple<int, int, int, bool>, TuneChoice> g_tune;   // (device, N, X, split) -> choice
 int g_tune_mode = 1;
 }  // namespace
 
@@ -669,7 +834,7 @@ int set_autotune(int mode)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     int old = g_tune_mode;
-    if (mode == 0 || mode == 1) g_tune_mode = mode;
+    if (mode == 0 || mode == 1 || mode == 2) g_tune_mode = mode;
     return old;
 }
 
@@ -680,7 +845,7 @@ static void apply_kper(TcPlanes &p, int kper)
     p.fwd_splits = (nk + kper - 1) / kper;
 }
 
-bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s)
+bool tc_autotune(TcPlanes &p, float2 *part, TabEntry *tab, float2 *v, cudaStream_t s)
 {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -688,9 +853,15 @@ bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s)
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         if (g_tune_mode == 0) return true;                      // heuristic split
+        if (g_tune_mode == 2) {                                 // heuristic split, fused forward
+            p.fwd_fused = !p.split;
+            return true;
+        }
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            apply_kper(p, it->second);
+            apply_kper(p, it->second.kper);
+            p.fwd_fused = it->second.fused;
+            for (int k = 0; k < 4; k++) p.tune_ms[k] = it->second.ms[k];
             return true;
         }
     }
@@ -729,6 +900,36 @@ bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s)
         }
         p.tuned++;
     }
+    TuneChoice ch;
+    ch.kper = best;
+    apply_kper(p, best);
+    // plain BF16: the separate synthesis pass (both operand sets, as an update runs it) plus the
+    // forward GEMM, against the back-projection's synthesis alone plus the fused forward, on
+    // tables holding covered entries (every entry then costs its full synthesis)
+    if (ok && !p.split && tab && v) {
+        ok = cudaMemsetAsync(tab, 0, sizeof(TabEntry) * (size_t)p.N * p.X, s) == cudaSuccess &&
+             cudaMemsetAsync(v, 0, sizeof(float2) * (size_t)p.X, s) == cudaSuccess;
+        const double f = 5e5, c0 = 1500.0;
+        auto timed = [&](auto &&launch) {
+            float tot = 0.f;
+            for (int rep = 0; rep < 3 && ok; rep++) {
+                ok = cudaEventRecord(a, s) == cudaSuccess;
+                launch();
+                ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(b, s) == cudaSuccess &&
+                     cudaEventSynchronize(b) == cudaSuccess;
+                float ms = 0.f;
+                ok = ok && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+                if (rep > 0) tot += ms * 0.5f;
+            }
+            return tot;
+        };
+        ch.ms[0] = timed([&] { launch_synth_both_tc(p, tab, v, f, c0, s); });
+        ch.ms[1] = timed([&] { launch_forward_tc(p, part, s); });
+        ch.ms[2] = timed([&] { launch_synth_bp_tc(p, tab, f, c0, s); });
+        ch.ms[3] = timed([&] { launch_forward_tc_fused(p, tab, v, f, c0, part, s); });
+        ch.fused = ok && ch.ms[2] + ch.ms[3] < ch.ms[0] + ch.ms[1];
+        p.tuned += 2;
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (!ok) return false;
@@ -736,9 +937,10 @@ bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s)
     if (cudaMemcpyAsync(p.err, &zero, sizeof zero, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return false;
-    apply_kper(p, best);
+    p.fwd_fused = ch.fused;
+    for (int k = 0; k < 4; k++) p.tune_ms[k] = ch.ms[k];
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune.emplace(key, best);
+    g_tune.emplace(key, ch);
     return true;
 }
 
@@ -762,6 +964,16 @@ void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, doub
     k_synth_fwd_tc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tab, v, p.N, p.X, p.Xpad, p.fwd_pstride, fhi, flo,
                                                                green_const_tc(f, c0),
                                                                static_cast<__nv_bfloat16 *>(p.fplanes), p.split);
+}
+
+int launch_forward_tc_fused(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, float2 *part,
+                            cudaStream_t s)
+{
+    const int T = p.Npad / BM, pairs = T * (T + 1) / 2;
+    const float fhi = (float)f, flo = (float)(f - (double)fhi);
+    k_forward_tc_fused<<<dim3(pairs, p.fwd_splits), 192, F_SMEM, s>>>(tab, v, p.N, p.X, T, p.Xpad / BK, p.fwd_kper,
+                                                                      fhi, flo, green_const_tc(f, c0), part, p.err);
+    return p.fwd_splits;
 }
 
 int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s)

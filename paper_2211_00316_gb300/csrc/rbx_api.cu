@@ -278,7 +278,7 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom, const double *
         if (w.tc.fwd_max_splits > w.fwd_splits) w.fwd_splits = w.tc.fwd_max_splits;
     }
     ALLOC(w.part, (size_t)w.fwd_splits * N * N);
-    if (g.precision != RBX_FP32 && !tc_autotune(w.tc, w.part, j->stream)) {
+    if (g.precision != RBX_FP32 && !tc_autotune(w.tc, w.part, w.tab, w.v, j->stream)) {
         cudaGetLastError();
         free_ws(w, j->stream);
         return fail(j, RBX_ECUDA, "autotuning of the tensor-core forward failed");
@@ -535,7 +535,18 @@ static rbx_status forward_core(rbx_job *j, double f, bool timed, bool both = fal
 {
     Workspace &w = j->w;
     rbx_status st;
-    if (j->g.precision != RBX_FP32) {
+    if (j->g.precision != RBX_FP32 && w.tc.fwd_fused) {
+        // the tuner's choice: the forward forms its operands from the tables; an update still
+        // writes the back-projection's planes
+        if (both) {
+            launch_synth_bp_tc(w.tc, w.tab, f, j->g.c0, j->stream);
+            LAUNCHED(j, 1);
+        }
+        if (timed && (st = record(j, EV_SYNTH_F))) return st;
+        int splits = launch_forward_tc_fused(w.tc, w.tab, w.v, f, j->g.c0, w.part, j->stream);
+        launch_forward_reduce(w.part, w.N, splits, w.D, j->stream);
+        LAUNCHED(j, 2);
+    } else if (j->g.precision != RBX_FP32) {
         if (both)
             launch_synth_both_tc(w.tc, w.tab, w.v, f, j->g.c0, j->stream);
         else
@@ -1097,6 +1108,15 @@ rbx_status rbx_get_tuning(const rbx_job *j, int *fwd_splits, int *candidates_tim
     if (!j) return RBX_EINVAL;
     if (fwd_splits) *fwd_splits = j->g.precision == RBX_FP32 ? j->w.fwd_splits : j->w.tc.fwd_splits;
     if (candidates_timed) *candidates_timed = j->w.tc.tuned;
+    return RBX_OK;
+}
+
+rbx_status rbx_get_tuning_times(const rbx_job *j, float *ms, int *fused)
+{
+    if (!j) return RBX_EINVAL;
+    if (ms)
+        for (int k = 0; k < 4; k++) ms[k] = j->w.tc.tune_ms[k];
+    if (fused) *fused = j->w.tc.fwd_fused ? 1 : 0;
     return RBX_OK;
 }
 

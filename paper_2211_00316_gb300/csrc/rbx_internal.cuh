@@ -69,6 +69,9 @@ struct TcPlanes {
     int fwd_splits = 1, fwd_kper = 1;
     int fwd_max_splits = 1;    // largest K split the autotuner may pick (sizes the partials)
     int tuned = 0;             // candidates timed for this job (0: heuristic or cached choice)
+    bool fwd_fused = false;    // the forward forms its operands from the tables (k_forward_tc_fused)
+    float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};   // tuner's times: both synthesis passes, forward GEMM,
+                                               // back-projection synthesis alone, fused forward
     bool split = false;        // split BF16: every plane set is followed by its lo set
     void *fplanes = nullptr;   // [4][Npad][Xpad] bf16: Gre, Gim, (Gv)re, (Gv)im
     void *bplanes = nullptr;   // [6][Xp][Npad] bf16: u, conj(kappa) u, kappa u (re, im)
@@ -165,11 +168,14 @@ void launch_backproject_simt(const float2 *A, const float2 *kap, const float2 *R
 bool tc_setup(TcPlanes &p, int N, int X, bool split, cudaStream_t s);
 // Choose the forward K split by timing the candidates on this job's planes (once per shape
 // and process; later jobs of the shape reuse the choice). part holds fwd_max_splits partials.
-bool tc_autotune(TcPlanes &p, float2 *part, cudaStream_t s);
+bool tc_autotune(TcPlanes &p, float2 *part, TabEntry *tab, float2 *v, cudaStream_t s);
 int set_autotune(int mode);
 void tc_free(TcPlanes &p, cudaStream_t s);
 void launch_synth_fwd_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s);
 int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s);
+// The forward with its operands formed from the tables in the contraction (no planes).
+int launch_forward_tc_fused(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, float2 *part,
+                            cudaStream_t s);
 void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, double f, double c0, cudaStream_t s);
 // a bounded wait on a barrier nothing signals (flag = 1 when it gave up)
 void launch_wait_selftest(unsigned *flag, cudaStream_t s);

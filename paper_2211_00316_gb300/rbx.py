@@ -86,6 +86,7 @@ _SIGS = {
     "rbx_set_linking": [_P, C.c_int],
     "rbx_update_set": [_P, C.POINTER(C.c_double), C.c_int, C.c_double, _P, C.POINTER(Stats)],
     "rbx_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "rbx_get_tuning_times": [_P, C.POINTER(C.c_float), C.POINTER(C.c_int)],
     "rbx_set_slot_timing": [_J, C.c_int],
     "rbx_selftest_bounded_wait": [C.POINTER(C.c_int)],
     "rbx_pool_usage": [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_int],
@@ -328,7 +329,10 @@ class Job:
     def tuning(self) -> dict:
         sp, nc = C.c_int(), C.c_int()
         self._check(self.L.rbx_get_tuning(self.h, C.byref(sp), C.byref(nc)))
-        return dict(fwd_splits=sp.value, candidates_timed=nc.value)
+        ms, fu = (C.c_float * 4)(), C.c_int()
+        self._check(self.L.rbx_get_tuning_times(self.h, ms, C.byref(fu)))
+        return dict(fwd_splits=sp.value, candidates_timed=nc.value, fused_forward=bool(fu.value),
+                    ms_synth_both=ms[0], ms_forward_gemm=ms[1], ms_synth_bp=ms[2], ms_forward_fused=ms[3])
 
     def sync(self):
         self._check(self.L.rbx_synchronize(self.h))

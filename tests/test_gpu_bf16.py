@@ -209,3 +209,44 @@ def test_update_synthesis_matches_forward_bits(case, prec):
     st = job.update_from_tables(case.f, 1e5, data)
     assert st["resid_norm2"] == 0.0
     job.set_model(dev(case.c32))
+
+
+@pytest.mark.parametrize("N,nx", [(72, 96), (300, 160)])
+def test_fused_synthesis_forward_is_bit_identical(N, nx, oracle_mod):
+    """The fused-synthesis forward (operand tiles formed from the tables inside the
+    contraction, the tuner's candidate) against the separate synthesis pass plus TMA-fed
+    planes, at the same heuristic split: the same BF16 operands, so the same D bit for bit,
+    and the same update, on rings that fill their 128-row tiles raggedly (72, 300). A job of a
+    new shape under the default tuning times both forms and keeps the faster."""
+    w = P.custom(N, nx, 0.9e-3, (nx - 1) * 0.9e-3 / 2 - 3e-3, kind="discs", freqs=(3e5,))
+    c32 = w.c_init.astype(np.float32)
+    f = 3e5
+    prev = rbx.autotune(1)
+    try:
+        outs, ups, tun = [], [], []
+        data, _ = oracle_mod.Oracle(w.geom).predict(f, w.c_true)
+        for mode in (0, 2):
+            rbx.autotune(mode)
+            j = rbx.Job()
+            j.set_geometry(w.geom, precision=rbx.RBX_BF16)
+            j.set_model(dev(c32))
+            j.trace_rays(f)
+            rng = np.random.default_rng(4)
+            dm = dev((rng.standard_normal((w.geom.ny, w.geom.nx)) * 1e-9).astype(np.float32))
+            outs.append(j.forward(f, dm).cpu().numpy())
+            tun.append(j.tuning())
+            j.update_frequency(f, 1e5, dev(data, torch.complex64))
+            ups.append(j.get_model().cpu().numpy())
+            j.close()
+        assert not tun[0]["fused_forward"] and tun[1]["fused_forward"]
+        np.testing.assert_array_equal(outs[1], outs[0])
+        np.testing.assert_array_equal(ups[1], ups[0])
+        rbx.autotune(1)
+        j = rbx.Job()
+        j.set_geometry(P.custom(N + 1, nx, 0.9e-3, (nx - 1) * 0.9e-3 / 2 - 3e-3).geom, precision=rbx.RBX_BF16)
+        t = j.tuning()
+        j.close()
+        assert t["ms_synth_both"] > 0 and t["ms_forward_gemm"] > 0 and t["ms_synth_bp"] > 0 and t["ms_forward_fused"] > 0
+        assert t["fused_forward"] == (t["ms_synth_bp"] + t["ms_forward_fused"] < t["ms_synth_both"] + t["ms_forward_gemm"])
+    finally:
+        rbx.autotune(prev)
