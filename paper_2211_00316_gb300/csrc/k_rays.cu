@@ -70,16 +70,6 @@ __device__ __forceinline__ void field_eval(const float *__restrict__ F, const Ra
     }
 }
 
-// Whether a step from (x, y) reads only nodes of the uniform medium: the block map of the
-// current fields (k_uniform_nbhd); a null map says no.
-__device__ __forceinline__ bool uniform_at(const RayParams &p, float x, float y)
-{
-    if (!p.ublk) return false;
-    const int i = clampi_((int)floorf((x - p.x0) * p.inv_dx), 0, p.nx - 1) / kUBlock;
-    const int j = clampi_((int)floorf((y - p.y0) * p.inv_dx), 0, p.ny - 1) / kUBlock;
-    return __ldg(p.ublk + (size_t)j * p.nbx + i) != 0;
-}
-
 // A ray sample as a triangle vertex.
 struct Vtx {
     float x, y, T, a, kx, ky;
@@ -203,10 +193,15 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
             float maxx = fmaxf(fmaxf(P00.x, P01.x), fmaxf(P10.x, P11.x));
             float miny = fminf(fminf(P00.y, P01.y), fminf(P10.y, P11.y));
             float maxy = fmaxf(fmaxf(P00.y, P01.y), fmaxf(P10.y, P11.y));
-            ix0 = max(0, (int)ceilf((minx - p.x0) * inv_dx));
-            int ix1 = min(p.nx - 1, (int)floorf((maxx - p.x0) * inv_dx));
-            iy0 = max(0, (int)ceilf((miny - p.y0) * inv_dx));
-            int iy1 = min(p.ny - 1, (int)floorf((maxy - p.y0) * inv_dx));
+            // candidate nodes of the bounding box, widened by 1e-3 cells: in FP32 the box's grid
+            // coordinates carry ~2e-5 cells of rounding, and a node that lies on a box edge (at a
+            // triangle's tip) must stay a candidate of every quad that may hold it; the edge
+            // functions below decide which does
+            const float slack = 1e-3f;
+            ix0 = max(0, (int)ceilf((minx - p.x0) * inv_dx - slack));
+            int ix1 = min(p.nx - 1, (int)floorf((maxx - p.x0) * inv_dx + slack));
+            iy0 = max(0, (int)ceilf((miny - p.y0) * inv_dx - slack));
+            int iy1 = min(p.ny - 1, (int)floorf((maxy - p.y0) * inv_dx + slack));
             w = ix1 - ix0 + 1;
             int h = iy1 - iy0 + 1;
             cnt = (w > 0 && h > 0) ? w * h : 0;
@@ -377,32 +372,14 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
     for (int i = 0; i < p.maxs; i++) {
         Vtx cur{};
         bool have = false;
-        if (alive && (i < kin || uniform_at(p, x, y))) {
-            // the step below in a uniform medium (every node it reads holds the medium of the
-            // water, so F1 still holds its fields): straight, p constant, dx += ds dp / n; a
-            // chord that crosses the ring ends there as in the step below
+        if (alive && i < kin) {
+            // the step below in a uniform medium: straight, p constant, dx += ds dp / n
             const float n = F1.n, in = rcp_nr(n);
             const float rp = rsqrtf(px * px + py * py), tx = px * rp, ty = py * rp;
-            float inc = hds * (F1.nr + F1.nr), incB = LOSSY ? hds * (F1.al + F1.al) : 0.f;
-            const float xn = x + ds * tx, yn = y + ds * ty;
-            const bool last = xn * xn + yn * yn >= R2;
-            if (last) {
-                const float b = x * tx + y * ty, cc = i == 0 ? 0.f : x * x + y * y - R2;
-                const float disc = b * b - cc;
-                float t = -b + sqrtf(disc > 0.f ? disc : 0.f);
-                t = fminf(fmaxf(t, 0.f), ds);
-                const float fr = t / ds;
-                x = x + t * tx; y = y + t * ty;
-                inc *= fr;
-                incB *= fr;
-                dxx += fr * (ds * (dpx * in)); dxy += fr * (ds * (dpy * in));
-                field_eval<LOSSY, RAW>(F, p, x, y, F1);
-            } else {
-                kadd(x, cx, ds * tx); kadd(y, cy, ds * ty);
-                kadd(dxx, cdx, ds * (dpx * in)); kadd(dxy, cdy, ds * (dpy * in));
-            }
-            kadd(T, Tc, inc);
-            if (LOSSY) kadd(B, Bc, incB);
+            kadd(x, cx, ds * tx); kadd(y, cy, ds * ty);
+            kadd(dxx, cdx, ds * (dpx * in)); kadd(dxy, cdy, ds * (dpy * in));
+            kadd(T, Tc, hds * (F1.nr + F1.nr));
+            if (LOSSY) kadd(B, Bc, hds * (F1.al + F1.al));
             const float J = dxx * ty - dxy * tx;
             if (i == 0) { sc1 = sqrtf(F1.nr * fabsf(J) / ds); Jlast = J; }
             else if (J * Jlast < 0.f) K++;
@@ -411,11 +388,6 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
             cur.a = sc1 * rsqrtf(F1.nr * fabsf(J));
             if (LOSSY) cur.a *= expf(-B);
             have = true;
-            if (last) {
-                alive = false;
-                if (lane < 31 || j == N - 1)
-                    exits[(size_t)e * (N - 1) + (j - 1)] = make_float4(atan2f(y, x), T, cur.a, (float)K);
-            }
         } else if (alive) {
             // stage 1 at x: normalise p to n(x), q_x = p/n, q_p = grad n
             const float n = F1.n, in = rcp_nr(n);
@@ -565,74 +537,34 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
     if (lane == 0 && *hq.cov) atomicAdd(&counters[0], (unsigned long long)*hq.cov);
 }
 
-// Whether node k holds the uniform medium of node (0, 0) (n, alpha and the integrated
-// slowness equal to node (0, 0)'s, all derivatives zero); never when node (0, 0) itself has a
-// non-zero derivative.
-__device__ __forceinline__ bool node_uniform(const float4 *__restrict__ F, const RayParams &p, int k)
-{
-    const size_t nxy = (size_t)p.nx * p.ny;
-    const float2 *F2 = reinterpret_cast<const float2 *>(F + nxy), *F3 = F2 + nxy;
-    const float4 u0 = F[0], a0 = F[k];
-    const float2 v0 = F2[0], v1 = F3[0], b0 = F2[k], b1 = F3[k];
-    const bool flat0 = u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && v0.x == 0.f && v0.y == 0.f;
-    return flat0 && a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && b0.x == 0.f && b0.y == 0.f &&
-           b1.x == v1.x && b1.y == v1.y;
-}
-
-// Largest radius of a node whose fields differ from the uniform medium of node (0, 0); +inf
-// when node (0, 0) itself is not uniform.
+// Largest radius of a node whose fields differ from the uniform medium of node (0, 0)
+// (n, alpha and the integrated slowness there, all derivatives zero); +inf when node (0, 0)
+// itself is not uniform.
 __global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsigned long long *ru)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.nx * p.ny) return;
-    if (!node_uniform(F, p, k)) {
+    const size_t nxy = (size_t)p.nx * p.ny;
+    const float2 *F2 = reinterpret_cast<const float2 *>(F + nxy), *F3 = F2 + nxy;
+    const float4 u0 = F[0], a0 = F[k];
+    const float2 v0 = F2[0], v1 = F3[0], b0 = F2[k], b1 = F3[k];
+    const float4 u1 = make_float4(v0.x, v0.y, v1.x, v1.y), a1 = make_float4(b0.x, b0.y, b1.x, b1.y);
+    if (k == 0 && !(u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && u1.x == 0.f && u1.y == 0.f)) {
+        atomicMax(ru, (unsigned long long)__float_as_uint(__int_as_float(0x7f800000)));
+        return;
+    }
+    const bool uni = a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f &&
+                     a1.z == u1.z && a1.w == u1.w;
+    if (!uni) {
         const float px = p.x0 + (float)(k % p.nx) * p.dx, py = p.y0 + (float)(k / p.nx) * p.dx;
-        const float r = node_uniform(F, p, 0) ? sqrtf(px * px + py * py) : __int_as_float(0x7f800000);
-        atomicMax(ru, (unsigned long long)__float_as_uint(r));
+        atomicMax(ru, (unsigned long long)__float_as_uint(sqrtf(px * px + py * py)));
     }
 }
 
-// bu[b] = 1 when every node of block b (kUBlock x kUBlock nodes, clipped at the grid's edge)
-// holds the uniform medium of node (0, 0).
-__global__ void k_uniform_blocks(const float4 *__restrict__ F, RayParams p, uint8_t *__restrict__ bu)
+void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= p.nbx * p.nby) return;
-    const int bx = b % p.nbx, by = b / p.nbx;
-    bool u = true;
-    for (int dy = 0; dy < kUBlock; dy++)
-        for (int dx = 0; dx < kUBlock; dx++) {
-            const int ix = bx * kUBlock + dx, iy = by * kUBlock + dy;
-            if (ix < p.nx && iy < p.ny) u = u && node_uniform(F, p, iy * p.nx + ix);
-        }
-    bu[b] = u ? 1 : 0;
-}
-
-// ub[b] = 1 when the blocks within hb block widths of block b (those inside the grid) are all
-// uniform. hb covers a step's reach: a Heun step from a sample evaluates the fields at the
-// sample, at an auxiliary point and at the next sample, all within ds of it, and each bilinear
-// evaluation reads the four nodes of its cell, within sqrt(2) dx; so from any point of a block
-// with ub = 1 the step reads only uniform nodes and is the closed-form straight step.
-__global__ void k_uniform_nbhd(const uint8_t *__restrict__ bu, RayParams p, int hb, uint8_t *__restrict__ ub)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= p.nbx * p.nby) return;
-    const int bx = b % p.nbx, by = b / p.nbx;
-    bool u = true;
-    for (int j = max(0, by - hb); j <= min(p.nby - 1, by + hb); j++)
-        for (int i = max(0, bx - hb); i <= min(p.nbx - 1, bx + hb); i++) u = u && bu[j * p.nbx + i];
-    ub[b] = u ? 1 : 0;
-}
-
-void launch_uniform_map(const float *fields, const RayParams &p, unsigned long long *ru, uint8_t *bu, uint8_t *ub,
-                        cudaStream_t s)
-{
-    const int n = p.nx * p.ny, nb = p.nbx * p.nby;
-    const float4 *F = reinterpret_cast<const float4 *>(fields);
-    k_uniform_radius<<<(n + 255) / 256, 256, 0, s>>>(F, p, ru);
-    k_uniform_blocks<<<(nb + 127) / 128, 128, 0, s>>>(F, p, bu);
-    const int hb = (int)ceil(((double)p.ds + 1.4142135623730951 * p.dx) / (kUBlock * (double)p.dx));
-    k_uniform_nbhd<<<(nb + 127) / 128, 128, 0, s>>>(bu, p, hb, ub);
+    const int n = p.nx * p.ny;
+    k_uniform_radius<<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float4 *>(fields), p, ru);
 }
 
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,

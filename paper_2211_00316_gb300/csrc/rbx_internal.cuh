@@ -28,16 +28,11 @@ struct __align__(16) TabEntry {
     float gam;      // ray direction angle [rad]
 };
 
-// Side, in nodes, of the blocks of the uniform-medium map the ray trace consults.
-constexpr int kUBlock = 4;
-
 struct RayParams {
     int N, X, nx, ny;
     float dx, x0, y0, R, ds, inv_dx, rmask;
     int maxs;
     const double *beta;   // [N] position angles of the transducers (device); nullptr: uniform ring 2 pi e / N
-    const uint8_t *ublk;  // [nby][nbx] blocks from which a ray step reads only uniform nodes; nullptr: none
-    int nbx, nby;         // blocks of kUBlock x kUBlock nodes per row and column
 };
 
 // 1/v for v finite and away from 0 and the denormal range (a slowness, a triangle's edge
@@ -99,8 +94,6 @@ struct Workspace {
     double *dmacc = nullptr;    // sum of a frequency set's search directions per mask node
     float4 *linked = nullptr;   // linked rays of the direct term [N][N] (0, T, a, K)
     double *beta = nullptr;     // [N] position angles of caller-placed transducers; nullptr: uniform ring
-    uint8_t *ublk = nullptr;    // uniform-medium block map of the current fields, and its per-block pass
-    uint8_t *ublk0 = nullptr;
     float2 *gdir = nullptr, *D = nullptr, *R = nullptr, *Rs = nullptr, *part = nullptr, *gpart = nullptr;
     float2 *data = nullptr;
     double *red = nullptr;           // reduction scratch
@@ -128,9 +121,7 @@ void launch_check_alpha(const float *a, int n, unsigned long long *flag, cudaStr
 void launch_fill(float *p, float v, size_t n, cudaStream_t s);
 
 // k_rays.cu
-// Largest radius of a non-uniform node (ru, float bits) and the block map p.ublk (bu: scratch).
-void launch_uniform_map(const float *fields, const RayParams &p, unsigned long long *ru, uint8_t *bu, uint8_t *ub,
-                        cudaStream_t s);
+void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s);
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
                          unsigned long long *counters, bool lossy, bool raw, cudaStream_t s);
 void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s);
