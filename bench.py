@@ -385,10 +385,16 @@ def batched_form(args, rbx, P, torch, pool=None, steps=None, warmup=None, varian
         out[name] = {"value": updates / float(np.mean(dev)), "unit": UNIT, "s_per_step_device": float(np.mean(dev)),
                      "s_per_step_wall": float(np.mean(wall))}
 
-    def sequential(jobs, data):
+    kernel_ms = {}
+
+    def sequential(jobs, data, tag):
         def run():
+            acc = {}
             for w, j, d in zip(pool, jobs, data):
-                j.reconstruct(w[0].freqs, d)
+                for st in j.reconstruct(w[0].freqs, d):
+                    for k, v in st["ms_kernel"].items():
+                        acc[k] = acc.get(k, 0.0) + v
+            kernel_ms[tag] = acc   # per-kernel device time of the step's updates, each run alone
         return run
 
     for prec, tag in ((rbx.RBX_BF16, "bf16"), (rbx.RBX_FP32, "fp32")):
@@ -400,7 +406,7 @@ def batched_form(args, rbx, P, torch, pool=None, steps=None, warmup=None, varian
         batch_run = lambda g: (lambda: rbx.batch_run(jobs, freqs, data, use_graph=g)[1])
         timed(f"graph_{tag}", jobs, batch_run(True))
         timed(f"streams_{tag}", jobs, batch_run(False))
-        timed(f"sequential_{tag}", jobs, sequential(jobs, data))
+        timed(f"sequential_{tag}", jobs, sequential(jobs, data, tag))
         out[f"device_bytes_{tag}"] = {"jobs_measured": int(used1 - used0 + data_bytes), "estimate": int(est)}
         for j in jobs:
             j.close()
@@ -410,6 +416,10 @@ def batched_form(args, rbx, P, torch, pool=None, steps=None, warmup=None, varian
     diffs = [float(np.sqrt(np.mean((a - b) ** 2))) for a, b in zip(models["graph_bf16"], models["sequential_fp32"])]
     same = all(np.array_equal(a, b) for a, b in zip(models["graph_bf16"], models["sequential_bf16"]))
     out["graph_bf16_over_sequential_fp32"] = out["graph_bf16"]["value"] / out["sequential_fp32"]["value"]
+    # where the device time of the slices' updates goes (each update run alone, BF16): shares
+    if "bf16" in kernel_ms:
+        tot = sum(kernel_ms["bf16"].values())
+        out["kernel_share_bf16"] = {k: v / tot for k, v in sorted(kernel_ms["bf16"].items(), key=lambda x: -x[1])}
     out["rms_dc_bf16_vs_fp32_m_s"] = {"max": max(diffs), "median": float(np.median(diffs))}
     # error against the true model on the mask after the sweep, per slice: initial, BF16, FP32
     errs = []
@@ -777,6 +787,7 @@ def main():
             "graph_bf16": batched["graph_bf16"], "sequential_bf16": batched["sequential_bf16"],
             "sequential_fp32": batched["sequential_fp32"],
             "graph_bf16_over_sequential_fp32": batched["graph_bf16_over_sequential_fp32"],
+            "kernel_share_bf16": batched.get("kernel_share_bf16"),
             "graph_equals_sequential_bf16": batched["graph_equals_sequential_bf16"],
             "rms_dc_bf16_vs_fp32_m_s": batched["rms_dc_bf16_vs_fp32_m_s"],
             "detail": batched}

@@ -225,13 +225,7 @@ rbx_status rbx_update_frequency_host(rbx_job *job, double freq_hz, double dfreq_
 
 /* Queue one update exactly as rbx_update_frequency does, without waiting for it: nothing is
  * copied to the host, so the call can be captured into a CUDA graph. Its scalar results go to
- * device stats slot `slot` (0..63) of the job; read them with rbx_get_stats. The update
- * consumes its tables: once its operand synthesis has read them, their re-initialisation for
- * the next trace is queued on a side stream of the job (ordered before the job's next trace,
- * rbx_set_tables, rbx_synchronize and rbx_destroy), so it overlaps the contractions; calls
- * that read tables (rbx_get_tables, rbx_forward, rbx_adjoint, rbx_predict,
- * rbx_update_from_tables) then need rbx_trace_rays first (RBX_ESTATE otherwise). The same
- * holds after rbx_batch_run and the served form, which queue their updates this way. */
+ * device stats slot `slot` (0..63) of the job; read them with rbx_get_stats. */
 rbx_status rbx_update_frequency_async(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_dev, int slot);
 
 /* Wait for the job's stream and return the scalar results kept in stats slot `slot`

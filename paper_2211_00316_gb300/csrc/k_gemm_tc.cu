@@ -926,7 +926,17 @@ bool tc_autotune(TcPlanes &p, float2 *part, TabEntry *tab, float2 *v, cudaStream
         ch.ms[0] = timed([&] { launch_synth_both_tc(p, tab, v, f, c0, s); });
         ch.ms[1] = timed([&] { launch_forward_tc(p, part, s); });
         ch.ms[2] = timed([&] { launch_synth_bp_tc(p, tab, f, c0, s); });
-        ch.ms[3] = timed([&] { launch_forward_tc_fused(p, tab, v, f, c0, part, s); });
+        // the fused form once; timed again only if it is not already twice the separate pass
+        float once = 0.f;
+        if (ok) {
+            ok = cudaEventRecord(a, s) == cudaSuccess;
+            launch_forward_tc_fused(p, tab, v, f, c0, part, s);
+            ok = ok && cudaGetLastError() == cudaSuccess && cudaEventRecord(b, s) == cudaSuccess &&
+                 cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&once, a, b) == cudaSuccess;
+        }
+        ch.ms[3] = once;
+        if (ok && once < 2.f * (ch.ms[0] + ch.ms[1]))
+            ch.ms[3] = timed([&] { launch_forward_tc_fused(p, tab, v, f, c0, part, s); });
         ch.fused = ok && ch.ms[2] + ch.ms[3] < ch.ms[0] + ch.ms[1];
         p.tuned += 2;
     }

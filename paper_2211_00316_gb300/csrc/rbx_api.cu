@@ -39,13 +39,6 @@ struct rbx_job {
     cudaEvent_t *slot_ev = nullptr;     // [kHistSlots][EV_COUNT] (rbx_set_slot_timing)
     long long slot_launches[kHistSlots] = {};
     long long launches = 0;
-    // Queued updates re-initialise the tables for the next trace on a side stream as soon as
-    // their last reader (the operand synthesis) has run, so the 16 B x N x X clear overlaps the
-    // contractions instead of preceding the next trace on the job's stream.
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_tab_dead = nullptr, ev_tab_clear = nullptr;
-    bool clear_early = false;          // the update being queued clears its tables after their last read
-    bool tab_clear_pending = false;    // a clear is queued on aux that the job's stream has not waited for
 };
 
 static rbx_status fail(rbx_job *j, rbx_status st, const char *fmt, ...)
@@ -139,29 +132,6 @@ static rbx_status record(rbx_job *j, int k)
 
 extern "C" {
 
-// Queue the all-ones re-initialisation of the tables on the side stream, after the job's
-// stream has passed their last read; the tables count as gone from then on.
-static rbx_status clear_tables_early(rbx_job *j)
-{
-    CUDA_TRY(j, cudaEventRecord(j->ev_tab_dead, j->stream));
-    CUDA_TRY(j, cudaStreamWaitEvent(j->aux, j->ev_tab_dead, 0));
-    CUDA_TRY(j, cudaMemsetAsync(j->w.tab, 0xff, sizeof(TabEntry) * (size_t)j->w.N * j->w.X, j->aux));
-    CUDA_TRY(j, cudaEventRecord(j->ev_tab_clear, j->aux));
-    j->tab_clear_pending = true;
-    j->has_tables = false;
-    return RBX_OK;
-}
-
-// Order the job's stream after a pending early clear of the tables.
-static rbx_status join_table_clear(rbx_job *j)
-{
-    if (j->tab_clear_pending) {
-        CUDA_TRY(j, cudaStreamWaitEvent(j->stream, j->ev_tab_clear, 0));
-        j->tab_clear_pending = false;
-    }
-    return RBX_OK;
-}
-
 rbx_status rbx_create(rbx_job **out, void *cuda_stream)
 {
     if (!out) return RBX_EINVAL;
@@ -176,13 +146,6 @@ rbx_status rbx_create(rbx_job **out, void *cuda_stream)
             return RBX_ECUDA;
         }
     }
-    // the side stream of early table clears (created here, never inside a stream capture)
-    if (cudaStreamCreateWithFlags(&j->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&j->ev_tab_dead, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&j->ev_tab_clear, cudaEventDisableTiming) != cudaSuccess) {
-        rbx_destroy(j);
-        return RBX_ECUDA;
-    }
     *out = j;
     return RBX_OK;
 }
@@ -190,16 +153,12 @@ rbx_status rbx_create(rbx_job **out, void *cuda_stream)
 rbx_status rbx_destroy(rbx_job *j)
 {
     if (!j) return RBX_EINVAL;
-    if (j->tab_clear_pending) cudaStreamWaitEvent(j->stream, j->ev_tab_clear, 0);
     cudaStreamSynchronize(j->stream);
     free_ws(j->w, j->stream);
     if (j->d_count) cudaFreeAsync(j->d_count, j->stream);
     cudaStreamSynchronize(j->stream);
     for (int k = 0; k < EV_COUNT; k++)
         if (j->ev[k]) cudaEventDestroy(j->ev[k]);
-    if (j->ev_tab_dead) cudaEventDestroy(j->ev_tab_dead);
-    if (j->ev_tab_clear) cudaEventDestroy(j->ev_tab_clear);
-    if (j->aux) cudaStreamDestroy(j->aux);
     if (j->slot_ev) {
         for (int k = 0; k < kHistSlots * EV_COUNT; k++)
             if (j->slot_ev[k]) cudaEventDestroy(j->slot_ev[k]);
@@ -214,8 +173,6 @@ const char *rbx_last_error(const rbx_job *j) { return j ? j->err.c_str() : "null
 rbx_status rbx_synchronize(rbx_job *j)
 {
     if (!j) return RBX_EINVAL;
-    rbx_status st = join_table_clear(j);
-    if (st) return st;
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     return RBX_OK;
 }
@@ -262,7 +219,6 @@ rbx_status rbx_set_geometry(rbx_job *j, const rbx_geometry *geom, const double *
              "transducer positions must run counterclockwise around the ring once, in index order");
     }
 
-    if (rbx_status st0 = join_table_clear(j)) return st0;
     CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     free_ws(j->w, j->stream);
     keep_pool_memory();
@@ -499,11 +455,7 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     j->ns_valid = false;   // recompute the fields for this model
     if ((st = smooth(j, f))) return st;
     if ((st = record(j, EV_FIELDS))) return st;
-    if (j->tab_clear_pending) {   // the last queued update cleared them on the side stream
-        if ((st = join_table_clear(j))) return st;
-    } else {
-        CUDA_TRY(j, cudaMemsetAsync(w.tab, 0xff, sizeof(TabEntry) * (size_t)w.N * w.X, j->stream));
-    }
+    CUDA_TRY(j, cudaMemsetAsync(w.tab, 0xff, sizeof(TabEntry) * (size_t)w.N * w.X, j->stream));
     CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
     const RayParams p = ray_params(j);
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
@@ -523,7 +475,6 @@ rbx_status rbx_set_tables(rbx_job *j, const float *T, const float *a, const floa
 {
     if (!j || !T || !a || !gam || !K || !exits) return RBX_EINVAL;
     NEED(j, j->has_geom, RBX_ESTATE, "rbx_set_tables before rbx_set_geometry");
-    if (rbx_status st0 = join_table_clear(j)) return st0;   // a pending clear must not overwrite them
     Workspace &w = j->w;
     size_t n = (size_t)w.N * w.X;
     CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
@@ -585,7 +536,6 @@ static rbx_status forward_core(rbx_job *j, double f, bool timed, bool both = fal
         }
         if (timed && (st = record(j, EV_SYNTH_F))) return st;
         int splits = launch_forward_tc_fused(w.tc, w.tab, w.v, f, j->g.c0, w.part, j->stream);
-        if (both && j->clear_early && (st = clear_tables_early(j))) return st;
         launch_forward_reduce(w.part, w.N, splits, w.D, j->stream);
         LAUNCHED(j, 2);
     } else if (j->g.precision != RBX_FP32) {
@@ -595,8 +545,6 @@ static rbx_status forward_core(rbx_job *j, double f, bool timed, bool both = fal
             launch_synth_fwd_tc(w.tc, w.tab, w.v, f, j->g.c0, j->stream);
         LAUNCHED(j, 1);
         if (timed && (st = record(j, EV_SYNTH_F))) return st;
-        // an update's last read of its tables (both contractions' operands are planes now)
-        if (both && j->clear_early && (st = clear_tables_early(j))) return st;
         int splits = launch_forward_tc(w.tc, w.part, j->stream);
         launch_forward_reduce(w.part, w.N, splits, w.D, j->stream);
         LAUNCHED(j, 2);
@@ -934,9 +882,7 @@ rbx_status rbx_update_frequency_async(rbx_job *j, double f, double df, const voi
     const long long l0 = j->launches;
     if (j->slot_ev) j->evp = j->slot_ev + (size_t)slot * EV_COUNT;   // this update's own events
     rbx_status st = rbx_trace_rays(j, f);
-    j->clear_early = true;
     if (!st) st = enqueue_update(j, f, df, static_cast<const float2 *>(data_dev), true, slot);
-    j->clear_early = false;
     j->evp = j->ev;
     j->slot_launches[slot] = j->launches - l0;
     return st;
@@ -1002,7 +948,7 @@ static rbx_status enqueue_sweep(rbx_job *j, const double *freqs, int nf, const v
         rbx_status st = rbx_update_frequency_async(j, freqs[n], df, d, n);
         if (st) return st;
     }
-    return join_table_clear(j);   // the sweep ends with the side stream joined (graph capture needs it)
+    return RBX_OK;
 }
 
 rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs, const int *nf,
@@ -1040,13 +986,8 @@ rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs
         for (int i = 0; i < n && st == RBX_OK; i++) {
             BTRY(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
             BTRY(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming));
-            // wait for work already queued on the job's own stream and its side stream, then run
-            // on the batch stream
+            // wait for work already queued on the job's own stream, then run on the batch stream
             BTRY(cudaStreamSynchronize(jobs[i]->stream));
-            if (jobs[i]->tab_clear_pending) {
-                BTRY(cudaEventSynchronize(jobs[i]->ev_tab_clear));
-                jobs[i]->tab_clear_pending = false;
-            }
             saved[i] = jobs[i]->stream;
             jobs[i]->stream = streams[i];
         }

@@ -109,38 +109,3 @@ def test_batch_reports_a_failure_inside_the_sweep():
     for j in jobs:
         j.close()
 
-
-@pytest.mark.parametrize("precision", [rbx.RBX_BF16, rbx.RBX_FP32])
-def test_queued_updates_clear_their_tables_on_the_side(precision):
-    """Queued updates re-initialise their tables for the next trace on the job's side stream
-    (BF16: once the operand synthesis has read them): three queued updates give the models of
-    three synchronous ones bit for bit, the consumed tables are refused until the next trace,
-    and a trace, tables injected right after a queued update, and a destroy all wait for the
-    side stream."""
-    w = P.custom(96, 120, 0.8e-3, 40e-3, kind="breast", seed=3, freqs=(2e5, 3e5, 4e5))
-    jobs, data = prepare([w], precision)
-    j, d = jobs[0], data[0]
-    sync = []
-    for q, f in enumerate(w.freqs):
-        j.update_frequency(float(f), 1e5, d[q])
-        sync.append(j.get_model().cpu().numpy())
-    j.set_model(torch.tensor(w.c_init, dtype=torch.float32, device="cuda"))
-    for q, f in enumerate(w.freqs):
-        j.update_frequency_async(float(f), 1e5, d[q], slot=q)
-    j.sync()
-    np.testing.assert_array_equal(j.get_model().cpu().numpy(), sync[-1])
-    if precision == rbx.RBX_BF16:
-        with pytest.raises(rbx.RbxError) as e:
-            j.get_tables()
-        assert e.value.status == 4
-    j.trace_rays(float(w.freqs[0]))
-    t = j.get_tables()
-    assert bool((t["a"] > 0).all())
-    # tables injected right after a queued update are not overwritten by its pending clear
-    j.update_frequency_async(float(w.freqs[1]), 1e5, d[1], slot=0)
-    j.set_tables(t["T"], t["a"], t["gam"], t["K"], t["exits"])
-    t2 = j.get_tables()
-    for k in ("T", "a", "gam", "K"):
-        assert torch.equal(t2[k], t[k])
-    j.update_frequency_async(float(w.freqs[2]), 1e5, d[2], slot=1)
-    j.close()
