@@ -49,6 +49,16 @@ __device__ __forceinline__ float phase_cycles_tc(float T, int K, float fhi, floa
     return r + 0.125f - 0.25f * (float)K;
 }
 
+// sin and cos of 2 pi ph (ph in cycles) for the BF16 operands: the phase taken to whole turns
+// ([-1/2, 1/2] cycles, [-pi, pi] rad) and the hardware sine / cosine, whose absolute error
+// there (about 4e-7) is far below the planes' resolution (2^-8 BF16, 2^-16 split BF16). Every
+// kernel that forms these operands uses it, so they agree bit for bit.
+__device__ __forceinline__ void sincos_turns_tc(float ph, float *s, float *c)
+{
+    const float r = ph - rintf(ph);
+    __sincosf(6.28318530717958647692f * r, s, c);
+}
+
 // G v with its rounding fixed (no contraction left to the compiler), so every kernel that
 // forms the forward operands gives the same bits
 __device__ __forceinline__ float gv_re(float gr, float gi, float2 v) { return __fmaf_rn(gr, v.x, -__fmul_rn(gi, v.y)); }
@@ -308,7 +318,7 @@ __global__ __launch_bounds__(192, 1) void k_forward_tc_fused(const TabEntry *__r
                             const TabEntry t = tab[(size_t)row * X + x];
                             if (t.idk != kUncovered) {
                                 float sn, cs;
-                                sincospif(2.f * phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &sn, &cs);
+                                sincos_turns_tc(phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &sn, &cs);
                                 gr = C * t.a * cs;
                                 gi = C * t.a * sn;
                             }
@@ -566,7 +576,7 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *_
     float gr = 0.f, gi = 0.f;
     if (t.idk != kUncovered) {
         float s, c;
-        sincospif(2.f * phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &s, &c);
+        sincos_turns_tc(phase_cycles_tc(t.T, (int)(t.idk & 0xffu), fhi, flo), &s, &c);
         gr = C * t.a * c;
         gi = C * t.a * s;
     }
@@ -638,7 +648,7 @@ __global__ __launch_bounds__(256, 6) void k_synth_tc(const TabEntry *__restrict_
             // kappa from the hardware sine / cosine (gamma lies in [-pi, pi], absolute error
             // ~1e-6, far below the BF16 planes' and the split planes' 2^-16 resolution)
             float sn, cs, sgm, cgm;
-            sincospif(2.f * phase_cycles_tc(t[k].T, (int)(t[k].idk & 0xffu), fhi, flo), &sn, &cs);
+            sincos_turns_tc(phase_cycles_tc(t[k].T, (int)(t[k].idk & 0xffu), fhi, flo), &sn, &cs);
             __sincosf(t[k].gam, &sgm, &cgm);
             const float A = dg * rcp_nr(C * t[k].a);
             gr = C * t[k].a * cs;
