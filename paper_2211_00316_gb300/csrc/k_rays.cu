@@ -364,6 +364,7 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
         }
     }
     const int i0 = __reduce_min_sync(FULL, has_ray ? kin : 0x7fffffff);
+    const float rm = p.rmask + 2.f * p.dx, rm2 = rm * rm;
     float sc1 = 0.f, Jlast = 0.f;   // sc1 = sqrt(n_1 |J_1| / ds): a_i = sc1 / sqrt(n_i |J_i|)
     int K = 0;
     bool alive = has_ray;
@@ -478,8 +479,30 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
         ncur.K = __shfl_down_sync(FULL, cur.K, 1);
         const bool nhave = __shfl_down_sync(FULL, (int)have, 1) != 0;
         const bool valid = i >= 1 && i >= i0 && have && nhave && lane < 31 && j + 1 <= N - 1;
-        raster_quad_warp(valid, prev, cur, nprev, ncur, ((uint32_t)j << 11 | (uint32_t)i) << 1, p, inv_dx, rows, fan,
-                         hq, counters);
+        // A quad beyond a line two cells outside the mask holds no mask node, in any medium:
+        // the edge functions accept only points of its two triangles, which lie in the convex
+        // hull of its corners, so when every corner q has u.q > rm for u the direction of the
+        // corners' sum, so does every accepted point, and |q| > rm. The warp skips the step's
+        // rasterisation when that holds for all its quads. The corners' own radii beyond rm
+        // are necessary for it and cheap, so the line test runs only when they hold for the
+        // whole warp (radii alone would not do: the cross edge of a wide tube can be a chord
+        // through the mask).
+        const bool ob = fmaf(cur.x, cur.x, cur.y * cur.y) > rm2 && fmaf(prev.x, prev.x, prev.y * prev.y) > rm2;
+        const bool nb = __shfl_down_sync(FULL, (int)ob, 1) != 0;
+        bool skip = __all_sync(FULL, !valid || (ob && nb));
+        if (skip) {
+            bool hs = true;
+            if (valid) {
+                const float gx = (prev.x + cur.x) + (nprev.x + ncur.x), gy = (prev.y + cur.y) + (nprev.y + ncur.y);
+                const float h = fminf(fminf(fmaf(gx, prev.x, gy * prev.y), fmaf(gx, cur.x, gy * cur.y)),
+                                      fminf(fmaf(gx, nprev.x, gy * nprev.y), fmaf(gx, ncur.x, gy * ncur.y)));
+                hs = h > 0.f && h * h > rm2 * fmaf(gx, gx, gy * gy);
+            }
+            skip = __all_sync(FULL, hs);
+        }
+        if (!skip)
+            raster_quad_warp(valid, prev, cur, nprev, ncur, ((uint32_t)j << 11 | (uint32_t)i) << 1, p, inv_dx, rows,
+                             fan, hq, counters);
         prev = cur;
         nprev = ncur;
         // Leaving through the uniform water: once a ray is beyond rho, moving outward, and so
