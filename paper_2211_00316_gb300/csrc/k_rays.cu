@@ -300,26 +300,28 @@ __device__ __forceinline__ void raster_quad_warp(bool valid, const Vtx &P00, con
 // Warps per block, each tracing the same rays of a neighbouring transducer; 20 warps per SM.
 constexpr int kFansPerBlock = 4;
 
+// The per-warp hit queues of a block (shared memory).
+struct BlockQueues {
+    int xi[kFansPerBlock][64];
+    unsigned long long key[kFansPerBlock][64];
+    float4 v[kFansPerBlock][64];
+    unsigned cov[kFansPerBlock];
+};
+
+// One block's work: warp `warp` of the fans of fan block `eblk` (fans 4 eblk .. 4 eblk + 3),
+// one warp per fan; `rows` (the mask's row ranges) and the queues' coverage counts are set up
+// by the caller. No block-wide barrier inside: a warp may return early.
 template <bool LOSSY, bool RAW>
-__global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trace_raster(const float *__restrict__ F, const int4 *__restrict__ rows_g,
-                                                         TabEntry *__restrict__ tab, float4 *__restrict__ exits,
-                                                         RayParams p, unsigned long long *counters)
+__device__ __forceinline__ void trace_block(const float *__restrict__ F, const int4 *rows, TabEntry *__restrict__ tab,
+                                            float4 *__restrict__ exits, const RayParams &p,
+                                            unsigned long long *counters, int warp, int eblk, BlockQueues &bq)
 {
     const unsigned FULL = 0xffffffffu;
-    extern __shared__ int4 rows[];                          // [ny] mask row ranges
-    __shared__ int q_xi[kFansPerBlock][64];
-    __shared__ unsigned long long q_key[kFansPerBlock][64];
-    __shared__ float4 q_v[kFansPerBlock][64];
-    __shared__ unsigned q_cov[kFansPerBlock];
-    for (int q = threadIdx.x; q < p.ny; q += blockDim.x) rows[q] = rows_g[q];
-    if (threadIdx.x < kFansPerBlock) q_cov[threadIdx.x] = 0u;
-    __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // the warps of a block trace the same 32 rays of neighbouring transducers: rotated by one
     // ring step, those rays stay within about a cell of one another, so their field gathers
     // share L1 lines
-    const int warp = blockIdx.x;
-    const int e = blockIdx.y * kFansPerBlock + wib;
+    const int e = eblk * kFansPerBlock + wib;
     const int N = p.N;
     const int nwarps = (N - 2 + 30) / 31;
     if (warp >= nwarps || e >= N) return;  // whole warp leaves together
@@ -327,7 +329,7 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
     const bool has_ray = j <= N - 1;
     TabEntry *fan = tab + (size_t)e * p.X;
     const float ds = p.ds, hds = 0.5f * p.ds, inv_dx = p.inv_dx, R2 = p.R * p.R;
-    HitQueue hq{q_xi[wib], q_key[wib], q_v[wib], &q_cov[wib], 0};
+    HitQueue hq{bq.xi[wib], bq.key[wib], bq.v[wib], &bq.cov[wib], 0};
 
     const double be = p.beta ? p.beta[e] : 2.0 * 3.14159265358979323846 * e / N;
     float x = (float)(p.R * cos(be)), y = (float)(p.R * sin(be));
@@ -560,6 +562,54 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
     if (lane == 0 && *hq.cov) atomicAdd(&counters[0], (unsigned long long)*hq.cov);
 }
 
+template <bool LOSSY, bool RAW>
+__global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trace_raster(const float *__restrict__ F, const int4 *__restrict__ rows_g,
+                                                         TabEntry *__restrict__ tab, float4 *__restrict__ exits,
+                                                         RayParams p, unsigned long long *counters)
+{
+    extern __shared__ int4 rows[];                          // [ny] mask row ranges
+    __shared__ BlockQueues bq;
+    for (int q = threadIdx.x; q < p.ny; q += blockDim.x) rows[q] = rows_g[q];
+    if (threadIdx.x < kFansPerBlock) bq.cov[threadIdx.x] = 0u;
+    __syncthreads();
+    trace_block<LOSSY, RAW>(F, rows, tab, exits, p, counters, blockIdx.x, blockIdx.y, bq);
+}
+
+// Persistent form of the trace over several jobs (the batched form). Each block takes the
+// next item from a device counter until the list is exhausted: items are numbered job by job
+// in the order of g.j, and within a job as the blocks of the per-job grid (warps fastest). An
+// item is one block of the per-job kernel. The job list is a kernel parameter, so that the
+// jobs' parameters stay in the constant bank (with them in shared memory the kernel spilled
+// and ran 5.8 % slower per item; this form costs 1.1 %).
+template <bool LOSSY, bool RAW>
+__global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trace_grouped(const __grid_constant__ TraceGroup g,
+                                                                                        int *next)
+{
+    extern __shared__ int4 rows[];   // [largest ny of the jobs]
+    __shared__ BlockQueues bq;
+    __shared__ int s_item, s_job;
+    for (;;) {
+        __syncthreads();   // the block's warps are done with the previous item
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(next, 1);
+            int jb = 0;
+            if (it < g.total)
+                while (jb + 1 < g.njobs && g.j[jb + 1].item0 <= it) jb++;
+            s_item = it;
+            s_job = jb;
+        }
+        __syncthreads();
+        const int it = s_item;
+        if (it >= g.total) return;   // uniform over the block
+        const TraceJob &J = g.j[s_job];
+        for (int q = threadIdx.x; q < J.p.ny; q += blockDim.x) rows[q] = J.rows[q];
+        if (threadIdx.x < kFansPerBlock) bq.cov[threadIdx.x] = 0u;
+        __syncthreads();
+        const int local = it - J.item0;
+        trace_block<LOSSY, RAW>(J.F, rows, J.tab, J.exits, J.p, J.counters, local % J.nwarps, local / J.nwarps, bq);
+    }
+}
+
 // Largest radius of a node whose fields differ from the uniform medium of node (0, 0)
 // (n, alpha and the integrated slowness there, all derivatives zero); +inf when node (0, 0)
 // itself is not uniform.
@@ -604,6 +654,47 @@ void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, f
         k_trace_raster<false, true><<<grd, 32 * kFansPerBlock, sm, s>>>(fields, rows, tab, exits, p, counters);
     else
         k_trace_raster<false, false><<<grd, 32 * kFansPerBlock, sm, s>>>(fields, rows, tab, exits, p, counters);
+}
+
+int trace_items(int N, int *nwarps)
+{
+    const int nw = (N - 2 + 30) / 31;
+    if (nwarps) *nwarps = nw;
+    return nw * ((N + kFansPerBlock - 1) / kFansPerBlock);
+}
+
+template <bool LOSSY, bool RAW>
+static int grouped_blocks_of(int max_ny)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_grouped<LOSSY, RAW>, 32 * kFansPerBlock,
+                                                      (size_t)max_ny * sizeof(int4)) != cudaSuccess)
+        return 0;
+    return sms * per_sm;
+}
+
+int trace_grouped_blocks(bool lossy, bool raw, int max_ny)
+{
+    if (lossy && raw) return grouped_blocks_of<true, true>(max_ny);
+    if (lossy) return grouped_blocks_of<true, false>(max_ny);
+    if (raw) return grouped_blocks_of<false, true>(max_ny);
+    return grouped_blocks_of<false, false>(max_ny);
+}
+
+void launch_trace_grouped(const TraceGroup &g, int max_ny, int blocks, int *next, bool lossy, bool raw, cudaStream_t s)
+{
+    const int grd = blocks < g.total ? blocks : g.total;
+    const size_t sm = (size_t)max_ny * sizeof(int4);
+    if (lossy && raw)
+        k_trace_grouped<true, true><<<grd, 32 * kFansPerBlock, sm, s>>>(g, next);
+    else if (lossy)
+        k_trace_grouped<true, false><<<grd, 32 * kFansPerBlock, sm, s>>>(g, next);
+    else if (raw)
+        k_trace_grouped<false, true><<<grd, 32 * kFansPerBlock, sm, s>>>(g, next);
+    else
+        k_trace_grouped<false, false><<<grd, 32 * kFansPerBlock, sm, s>>>(g, next);
 }
 
 // rows[iy] = (compact index of the row's first mask node, first ix, last ix); empty rows

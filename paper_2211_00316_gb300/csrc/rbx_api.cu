@@ -2,6 +2,7 @@
 // Hessian-free update (declared in include/rbx.h).
 #include "rbx_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -38,6 +39,7 @@ struct rbx_job {
     cudaEvent_t *evp = nullptr;         // the event set record() writes: ev, or a slot's set
     cudaEvent_t *slot_ev = nullptr;     // [kHistSlots][EV_COUNT] (rbx_set_slot_timing)
     long long slot_launches[kHistSlots] = {};
+    long long slot_l0 = 0;     // launch count when the update being queued began
     long long launches = 0;
 };
 
@@ -444,11 +446,11 @@ static rbx_status ensure_dgamma(rbx_job *j)
     return RBX_OK;
 }
 
-rbx_status rbx_trace_rays(rbx_job *j, double f)
+// The trace of step a2/a3 in three parts, so that the batched form can run the middle one
+// for all its jobs as one grouped launch: the fields and the cleared tables, the ray trace
+// with its rasteriser, and the tables' bookkeeping.
+static rbx_status trace_begin(rbx_job *j, double f)
 {
-    if (!j) return RBX_EINVAL;
-    NEED(j, j->has_geom, RBX_ESTATE, "rbx_trace_rays before rbx_set_geometry");
-    NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
     Workspace &w = j->w;
     rbx_status st;
     if ((st = record(j, EV_START))) return st;
@@ -457,17 +459,40 @@ rbx_status rbx_trace_rays(rbx_job *j, double f)
     if ((st = record(j, EV_FIELDS))) return st;
     CUDA_TRY(j, cudaMemsetAsync(w.tab, 0xff, sizeof(TabEntry) * (size_t)w.N * w.X, j->stream));
     CUDA_TRY(j, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned long long), j->stream));
-    const RayParams p = ray_params(j);
     CUDA_TRY(j, cudaMemsetAsync(w.counters + 7, 0, sizeof(unsigned long long), j->stream));
-    launch_uniform_radius(w.fields, p, w.counters + 7, j->stream);
-    launch_trace_raster(w.fields, w.rows, w.tab, w.exits, p, w.counters, j->lossy, j->raw, j->stream);
+    launch_uniform_radius(w.fields, ray_params(j), w.counters + 7, j->stream);
+    LAUNCHED(j, 1);
+    return RBX_OK;
+}
+
+static rbx_status trace_launch(rbx_job *j)
+{
+    Workspace &w = j->w;
+    launch_trace_raster(w.fields, w.rows, w.tab, w.exits, ray_params(j), w.counters, j->lossy, j->raw, j->stream);
+    LAUNCHED(j, 1);
+    return RBX_OK;
+}
+
+static rbx_status trace_end(rbx_job *j)
+{
+    rbx_status st;
     j->linked_valid = j->dg_valid = false;
-    LAUNCHED(j, 2);
     if ((st = record(j, EV_TRACE))) return st;
     if (j->g.precision == RBX_FP32 && (st = ensure_dgamma(j))) return st;
     if ((st = record(j, EV_TABLES))) return st;
     j->has_tables = true;
     return RBX_OK;
+}
+
+rbx_status rbx_trace_rays(rbx_job *j, double f)
+{
+    if (!j) return RBX_EINVAL;
+    NEED(j, j->has_geom, RBX_ESTATE, "rbx_trace_rays before rbx_set_geometry");
+    NEED(j, !bad_freq(f), RBX_EINVAL, "frequency must be finite and > 0");
+    rbx_status st;
+    if ((st = trace_begin(j, f))) return st;
+    if ((st = trace_launch(j))) return st;
+    return trace_end(j);
 }
 
 rbx_status rbx_set_tables(rbx_job *j, const float *T, const float *a, const float *gam, const uint8_t *K,
@@ -873,19 +898,39 @@ rbx_status rbx_update_frequency_host(rbx_job *j, double f, double df, const void
     return RBX_OK;
 }
 
-rbx_status rbx_update_frequency_async(rbx_job *j, double f, double df, const void *data_dev, int slot)
+// rbx_update_frequency_async in two halves around the ray trace's launch (the batched form's
+// grouped trace goes between them).
+static rbx_status update_async_begin(rbx_job *j, double f, double df, const void *data_dev, int slot)
 {
     if (!j || !data_dev) return RBX_EINVAL;
     NEED(j, j->has_geom, RBX_ESTATE, "rbx_update_frequency_async before rbx_set_geometry");
     NEED(j, !bad_freq(f) && std::isfinite(df) && df > 0, RBX_EINVAL, "frequency and spacing must be finite and > 0");
     NEED(j, slot >= 0 && slot < kHistSlots, RBX_EINVAL, "stats slot must be in [0, 64)");
-    const long long l0 = j->launches;
+    j->slot_l0 = j->launches;
     if (j->slot_ev) j->evp = j->slot_ev + (size_t)slot * EV_COUNT;   // this update's own events
-    rbx_status st = rbx_trace_rays(j, f);
+    rbx_status st = trace_begin(j, f);
+    if (st) j->evp = j->ev;
+    return st;
+}
+
+static rbx_status update_async_end(rbx_job *j, double f, double df, const void *data_dev, int slot)
+{
+    rbx_status st = trace_end(j);
     if (!st) st = enqueue_update(j, f, df, static_cast<const float2 *>(data_dev), true, slot);
     j->evp = j->ev;
-    j->slot_launches[slot] = j->launches - l0;
+    j->slot_launches[slot] = j->launches - j->slot_l0;
     return st;
+}
+
+rbx_status rbx_update_frequency_async(rbx_job *j, double f, double df, const void *data_dev, int slot)
+{
+    rbx_status st = update_async_begin(j, f, df, data_dev, slot);
+    if (st) return st;
+    if ((st = trace_launch(j))) {
+        j->evp = j->ev;
+        return st;
+    }
+    return update_async_end(j, f, df, data_dev, slot);
 }
 
 rbx_status rbx_set_slot_timing(rbx_job *j, int on)
@@ -973,6 +1018,15 @@ rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs
     rbx_status st = RBX_OK;
     bool capturing = false;
     if (!streams || !joins || !saved) st = RBX_ENOMEM;
+    // the grouped trace needs one instantiation of the trace for all jobs
+    bool grouped = (use_graph & RBX_BATCH_GROUPED) != 0;
+    for (int i = 1; i < n; i++)
+        if (jobs[i]->lossy != j0->lossy || jobs[i]->raw != j0->raw) grouped = false;
+    int maxnf = 0, max_ny = 0, gblocks = 0;
+    std::vector<TraceGroup> groups;   // launches of step q: groups[gfirst[q] .. gfirst[q + 1])
+    std::vector<int> gfirst;
+    int *next_dev = nullptr;          // one work counter per launch
+    cudaEvent_t trev = nullptr;
 #define BTRY(call)                                                                                       \
     do {                                                                                                 \
         cudaError_t e_ = (call);                                                                         \
@@ -992,25 +1046,113 @@ rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs
             jobs[i]->stream = streams[i];
         }
     }
+    if (st == RBX_OK && grouped) {
+        // work lists of the grouped traces, one per sweep step q: the jobs still sweeping,
+        // longest in-mask ray paths (mask radius over step length) first, so that the list
+        // ends with the cheapest items; kMaxGroup jobs per launch
+        std::vector<int> order(n);
+        for (int i = 0; i < n; i++) {
+            order[i] = i;
+            maxnf = std::max(maxnf, nf[i]);
+            max_ny = std::max(max_ny, jobs[i]->w.ny);
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return jobs[a]->g.mask_radius / jobs[a]->g.ds > jobs[b]->g.mask_radius / jobs[b]->g.ds;
+        });
+        for (int q = 0; q < maxnf; q++) {
+            gfirst.push_back((int)groups.size());
+            for (int i : order) {
+                if (q >= nf[i]) continue;
+                if (groups.size() == (size_t)gfirst.back() || groups.back().njobs == kMaxGroup) {
+                    groups.emplace_back();
+                    std::memset(&groups.back(), 0, sizeof(TraceGroup));
+                }
+                TraceGroup &gr = groups.back();
+                const Workspace &w = jobs[i]->w;
+                TraceJob &t = gr.j[gr.njobs++];
+                t.F = w.fields; t.rows = w.rows; t.tab = w.tab; t.exits = w.exits; t.counters = w.counters;
+                t.p = ray_params(jobs[i]);
+                t.item0 = gr.total;
+                gr.total += trace_items(w.N, &t.nwarps);
+            }
+        }
+        gfirst.push_back((int)groups.size());
+        gblocks = trace_grouped_blocks(j0->lossy, j0->raw, max_ny);
+        if (gblocks < 1) st = fail(j0, RBX_ECUDA, "no resident block for the grouped trace");
+        BTRY(cudaMalloc(&next_dev, sizeof(int) * groups.size()));
+        BTRY(cudaEventCreateWithFlags(&trev, cudaEventDisableTiming));
+    }
     if (st == RBX_OK) {
-        if (use_graph) {
+        if (use_graph & RBX_BATCH_GRAPH) {
             BTRY(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
             capturing = st == RBX_OK;
         } else {
             BTRY(cudaEventRecord(t0, origin));
         }
         BTRY(cudaEventRecord(fork, origin));
-        for (int i = 0; i < n && st == RBX_OK; i++) {
-            BTRY(cudaStreamWaitEvent(streams[i], fork, 0));
-            if (st == RBX_OK) {
-                rbx_status s2 = enqueue_sweep(jobs[i], freqs[i], nf[i], data_dev[i]);
-                if (s2 != RBX_OK) {
+        if (!grouped) {
+            for (int i = 0; i < n && st == RBX_OK; i++) {
+                BTRY(cudaStreamWaitEvent(streams[i], fork, 0));
+                if (st == RBX_OK) {
+                    rbx_status s2 = enqueue_sweep(jobs[i], freqs[i], nf[i], data_dev[i]);
+                    if (s2 != RBX_OK) {
+                        st = s2;
+                        if (jobs[i] != j0) j0->err = jobs[i]->err;
+                    }
+                }
+                BTRY(cudaEventRecord(joins[i], streams[i]));
+                BTRY(cudaStreamWaitEvent(origin, joins[i], 0));
+            }
+        } else {
+            // Lock-step by sweep step: each job queues its fields and cleared tables on its own
+            // stream, one persistent launch on the origin stream traces all of them, and each
+            // job queues the rest of its update after it. Only the trace is shared: a job's
+            // contractions and update overlap the other jobs' and its next step's fields.
+            for (int i = 0; i < n; i++) BTRY(cudaStreamWaitEvent(streams[i], fork, 0));
+            auto job_fail = [&](int i, rbx_status s2) {
+                if (st == RBX_OK) {
                     st = s2;
                     if (jobs[i] != j0) j0->err = jobs[i]->err;
                 }
+            };
+            for (int q = 0; q < maxnf && st == RBX_OK; q++) {
+                int first = -1;
+                for (int i = 0; i < n && st == RBX_OK; i++) {
+                    if (q >= nf[i]) continue;
+                    if (first < 0) first = i;
+                    const double df = sweep_df(freqs[i], nf[i], q);
+                    if (!(std::isfinite(df) && df > 0)) {
+                        job_fail(i, fail(jobs[i], RBX_EINVAL, "frequencies must increase"));
+                        break;
+                    }
+                    const float2 *d = static_cast<const float2 *>(data_dev[i]) + (size_t)q * jobs[i]->w.N * jobs[i]->w.N;
+                    rbx_status s2 = update_async_begin(jobs[i], freqs[i][q], df, d, q);
+                    if (s2 != RBX_OK) job_fail(i, s2);
+                    BTRY(cudaEventRecord(joins[i], streams[i]));
+                    BTRY(cudaStreamWaitEvent(origin, joins[i], 0));
+                }
+                if (st != RBX_OK) break;
+                for (int k = gfirst[q]; k < gfirst[q + 1] && st == RBX_OK; k++) {
+                    BTRY(cudaMemsetAsync(next_dev + k, 0, sizeof(int), origin));
+                    launch_trace_grouped(groups[k], max_ny, gblocks, next_dev + k, j0->lossy, j0->raw, origin);
+                    BTRY(cudaGetLastError());
+                    jobs[first]->launches += 1;   // one launch for up to kMaxGroup jobs' traces
+                }
+                BTRY(cudaEventRecord(trev, origin));
+                for (int i = 0; i < n && st == RBX_OK; i++) {
+                    if (q >= nf[i]) continue;
+                    BTRY(cudaStreamWaitEvent(streams[i], trev, 0));
+                    const double df = sweep_df(freqs[i], nf[i], q);
+                    const float2 *d = static_cast<const float2 *>(data_dev[i]) + (size_t)q * jobs[i]->w.N * jobs[i]->w.N;
+                    rbx_status s2 = update_async_end(jobs[i], freqs[i][q], df, d, q);
+                    if (s2 != RBX_OK) job_fail(i, s2);
+                }
             }
-            BTRY(cudaEventRecord(joins[i], streams[i]));
-            BTRY(cudaStreamWaitEvent(origin, joins[i], 0));
+            for (int i = 0; i < n; i++) {
+                jobs[i]->evp = jobs[i]->ev;
+                BTRY(cudaEventRecord(joins[i], streams[i]));
+                BTRY(cudaStreamWaitEvent(origin, joins[i], 0));
+            }
         }
         if (capturing) {
             cudaError_t e = cudaStreamEndCapture(origin, &graph);
@@ -1047,6 +1189,8 @@ rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs
         if (joins && joins[i]) cudaEventDestroy(joins[i]);
     }
     if (fork) cudaEventDestroy(fork);
+    if (trev) cudaEventDestroy(trev);
+    if (next_dev) cudaFree(next_dev);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (origin) cudaStreamDestroy(origin);

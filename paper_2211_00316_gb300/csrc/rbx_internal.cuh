@@ -124,6 +124,30 @@ void launch_fill(float *p, float v, size_t n, cudaStream_t s);
 void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s);
 void launch_trace_raster(const float *fields, const int4 *rows, TabEntry *tab, float4 *exits, const RayParams &p,
                          unsigned long long *counters, bool lossy, bool raw, cudaStream_t s);
+// One job of a persistent grouped trace (the batched form): its buffers and ray parameters,
+// and the range of work items it owns, [item0, item0 + nwarps * ceil(N / 4)).
+struct TraceJob {
+    const float *F;
+    const int4 *rows;
+    TabEntry *tab;
+    float4 *exits;
+    unsigned long long *counters;
+    RayParams p;
+    int item0, nwarps;
+};
+// Up to kMaxGroup jobs of one grouped trace launch, item0 ascending from 0; total = all items.
+constexpr int kMaxGroup = 64;
+struct TraceGroup {
+    int njobs, total;
+    TraceJob j[kMaxGroup];
+};
+// Work items of a job in the grouped trace (the per-job kernel's blocks).
+int trace_items(int N, int *nwarps);
+// Resident blocks of the grouped trace on this device (its grid).
+int trace_grouped_blocks(bool lossy, bool raw, int max_ny);
+// The traces of g's jobs as one persistent launch of `blocks` blocks taking items from *next
+// (zeroed by the caller).
+void launch_trace_grouped(const TraceGroup &g, int max_ny, int blocks, int *next, bool lossy, bool raw, cudaStream_t s);
 void launch_mask_rows(const int *node2x, int nx, int ny, int4 *rows, cudaStream_t s);
 // secant-linked rays of the direct term, linked[e][r] = (0, T, a, K) (maxit new rays per pair at
 // most), and the direct Green's function of one frequency from them

@@ -338,8 +338,12 @@ class Job:
         self._check(self.L.rbx_synchronize(self.h))
 
 
-def batch_run(jobs: list, freqs: list, data: list, use_graph: bool = True):
-    """Batched form (rbx_batch_run): every job's sweep on its own stream, one CUDA graph.
+RBX_BATCH_GRAPH, RBX_BATCH_GROUPED = 1, 2
+
+
+def batch_run(jobs: list, freqs: list, data: list, use_graph: bool = True, grouped: bool = False):
+    """Batched form (rbx_batch_run): every job's sweep on its own stream, optionally one CUDA
+    graph (use_graph) and one persistent trace launch per sweep step for all jobs (grouped).
     Returns (per-job last-update stats, device milliseconds of the whole batch)."""
     n = len(jobs)
     L = load()
@@ -350,7 +354,8 @@ def batch_run(jobs: list, freqs: list, data: list, use_graph: bool = True):
     dptrs = (C.c_void_p * n)(*[_ptr(d) for d in data])
     last = (Stats * n)()
     ms = C.c_float(0.0)
-    st = L.rbx_batch_run(handles, n, fptrs, nf, dptrs, int(use_graph), last, C.byref(ms))
+    flags = (RBX_BATCH_GRAPH if use_graph else 0) | (RBX_BATCH_GROUPED if grouped else 0)
+    st = L.rbx_batch_run(handles, n, fptrs, nf, dptrs, flags, last, C.byref(ms))
     if st != 0:
         raise RbxError(st, L.rbx_last_error(jobs[0].h).decode())
     return [s.as_dict() for s in last], ms.value
