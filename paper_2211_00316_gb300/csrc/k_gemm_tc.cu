@@ -589,6 +589,34 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *_
     put_split(planes + 3 * pstride + o, lo ? lo + 3 * pstride + o : nullptr, gv_im(gr, gi, vv));
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only), and its group fences.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// One synthesis tile: 32 nodes x 32 transducers, with a halo row of transducers on each side.
+constexpr int kSynSlots = 34 * 32;   // slot s holds row (e0 - 1 + s) mod N, nodes x0 .. x0 + 31
+
+// Queue the copies of tile t's table entries into buf (entries past the last node are not
+// copied; the consumer treats them as uncovered).
+__device__ __forceinline__ void synth_tile_load(const TabEntry *__restrict__ tab, int N, int X, int XT, int t,
+                                                TabEntry *buf)
+{
+    const int x0 = (t % XT) * 32, e0 = (t / XT) * 32;
+    for (int idx = threadIdx.x; idx < kSynSlots; idx += 256) {
+        const int slot = idx >> 5, x = x0 + (idx & 31);
+        if (x < X) {
+            const int e = (e0 - 1 + slot + N) % N;
+            cp_async16(buf + idx, tab + (size_t)e * X + x);
+        }
+    }
+}
+
 // planes [6][Xp][Npad] at [x][e]: u, conj(kappa) u, kappa u (re, im each);
 // u_e[x] = dgamma / (C a) exp(-i 2 pi (f T - K/4 + 1/8)), kappa = exp(i gamma).
 // The angular density dgamma (step a4) is formed here from the direction angles of the
@@ -596,100 +624,92 @@ __global__ void k_synth_fwd_tc(const TabEntry *__restrict__ tab, const float2 *_
 // around the ring), so the tables are read once more by 1/16 instead of a separate pass.
 // With FWD the same pass also writes the forward's planes (those of k_synth_fwd_tc, from the
 // same phase): an update reads its tables once for both contractions' operands.
+// Persistent: each block walks the tiles t = blockIdx.x, + gridDim.x, ... (nodes fastest) with
+// two shared-memory buffers, the next tile's entries copied in while the current one is
+// formed and stored, so that table reads stay in flight between the blocks' barriers.
 template <bool FWD, bool SPLIT>
-__global__ __launch_bounds__(256, 6) void k_synth_tc(const TabEntry *__restrict__ tab, int N, int X, int Npad,
+__global__ __launch_bounds__(256, SPLIT ? 3 : 4) void k_synth_tc(const TabEntry *__restrict__ tab, int N, int X, int Npad,
                                                      size_t pstride, float fhi, float flo, float C,
                                                      __nv_bfloat16 *__restrict__ planes, const float2 *__restrict__ bw,
-                                                     int Xpad, size_t fpstride, __nv_bfloat16 *__restrict__ fplanes)
+                                                     int Xpad, size_t fpstride, __nv_bfloat16 *__restrict__ fplanes,
+                                                     int XT, int ntiles)
 {
     constexpr int NPL = SPLIT ? 12 : 6;                      // back-projection planes (hi, then lo)
-    __shared__ __align__(16) __nv_bfloat16 sv[NPL][32][34];  // [plane][x][e]: rows of 17 words
-    __shared__ float sg[34][32];            // gamma of rows e0 - 1 .. e0 + 32 (mod N)
-    __shared__ unsigned char sc[34][32];    // covered flags of the same
-    const int x0 = blockIdx.x * 32, e0 = blockIdx.y * 32;
+    extern __shared__ __align__(16) unsigned char syn_smem[];
+    TabEntry *buf = reinterpret_cast<TabEntry *>(syn_smem);  // [2][kSynSlots]
+    // [plane][x][e]: rows of 17 words, the tile transposed and rounded to BF16
+    __nv_bfloat16(*sv)[32][34] = reinterpret_cast<__nv_bfloat16(*)[32][34]>(syn_smem + 2 * kSynSlots * sizeof(TabEntry));
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    const int x = x0 + tx;
-    TabEntry t[4];
+    int t = blockIdx.x, b = 0;
+    if (t < ntiles) synth_tile_load(tab, N, X, XT, t, buf);
+    cp_async_commit();
+    for (; t < ntiles; t += gridDim.x, b ^= 1) {
+        if (t + (int)gridDim.x < ntiles) synth_tile_load(tab, N, X, XT, t + gridDim.x, buf + (b ^ 1) * kSynSlots);
+        cp_async_commit();
+        cp_async_wait1();   // this thread's copies of tile t have landed
+        __syncthreads();    // and every thread's
+        const TabEntry *B = buf + b * kSynSlots;
+        const int x0 = (t % XT) * 32, e0 = (t / XT) * 32;
+        const int x = x0 + tx;
+        const bool xin = x < X;
+        float2 vv = make_float2(0.f, 0.f);
+        if (FWD && xin) vv = bw[x];   // Born weights of node x
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        // slot q + 1 holds row (e0 + q) mod N: past the last transducer (ragged last tile) it
-        // is the ring's wrap, row 0 being the next neighbour of row N - 1
-        const int q = ty + 8 * k, e = e0 + q;
-        TabEntry r;
-        r.idk = kUncovered;
-        r.T = r.a = r.gam = 0.f;
-        if (x < X) r = tab[(size_t)(e % N) * X + x];
-        sg[q + 1][tx] = r.gam;
-        sc[q + 1][tx] = r.idk != kUncovered;
-        if (e >= N) r.idk = kUncovered;   // not a row of this tile's output
-        t[k] = r;
-    }
-    if (ty < 2) {   // halo rows: slot 0 is row (e0 - 1) mod N, slot 33 row (e0 + 32) mod N
-        const int slot = ty == 0 ? 0 : 33;
-        const int e = (int)(((long long)e0 - 1 + slot + N) % N);
-        TabEntry h;
-        h.idk = kUncovered;
-        h.gam = 0.f;
-        if (x < X) h = tab[(size_t)e * X + x];
-        sg[slot][tx] = h.gam;
-        sc[slot][tx] = h.idk != kUncovered;
-    }
-    __syncthreads();
-    float2 vv = make_float2(0.f, 0.f);
-    if (FWD && x < X) vv = bw[x];   // Born weights of node x
+        for (int k = 0; k < 4; k++) {
+            const int q = ty + 8 * k;
+            float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float gr = 0.f, gi = 0.f;
+            const TabEntry r = B[(q + 1) * 32 + tx];   // row e0 + q
+            if (xin && e0 + q < N && r.idk != kUncovered) {
+                // slot q + 2 is row (e + 1) mod N and slot q row (e - 1) mod N, also for e = 0, N - 1
+                const TabEntry &rp = B[(q + 2) * 32 + tx], &rm = B[q * 32 + tx];
+                const float dg = (rp.idk != kUncovered && rm.idk != kUncovered) ? dgamma_of(rp.gam, rm.gam) : 0.f;
+                // kappa from the hardware sine / cosine (gamma lies in [-pi, pi], absolute error
+                // ~1e-6, far below the BF16 planes' and the split planes' 2^-16 resolution)
+                float sn, cs, sgm, cgm;
+                sincos_turns_tc(phase_cycles_tc(r.T, (int)(r.idk & 0xffu), fhi, flo), &sn, &cs);
+                __sincosf(r.gam, &sgm, &cgm);
+                const float A = dg * rcp_nr(C * r.a);
+                gr = C * r.a * cs;
+                gi = C * r.a * sn;
+                float ur = A * cs, ui = -A * sn;
+                v[0] = ur; v[1] = ui;
+                v[2] = cgm * ur + sgm * ui; v[3] = cgm * ui - sgm * ur;   // conj(kappa) u
+                v[4] = cgm * ur - sgm * ui; v[5] = cgm * ui + sgm * ur;   // kappa u
+            }
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int q = ty + 8 * k;
-        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float gr = 0.f, gi = 0.f;
-        if (t[k].idk != kUncovered) {
-            // slot q + 2 is row (e + 1) mod N and slot q row (e - 1) mod N, also for e = 0, N - 1
-            const float dg = (sc[q + 2][tx] && sc[q][tx]) ? dgamma_of(sg[q + 2][tx], sg[q][tx]) : 0.f;
-            // kappa from the hardware sine / cosine (gamma lies in [-pi, pi], absolute error
-            // ~1e-6, far below the BF16 planes' and the split planes' 2^-16 resolution)
-            float sn, cs, sgm, cgm;
-            sincos_turns_tc(phase_cycles_tc(t[k].T, (int)(t[k].idk & 0xffu), fhi, flo), &sn, &cs);
-            __sincosf(t[k].gam, &sgm, &cgm);
-            const float A = dg * rcp_nr(C * t[k].a);
-            gr = C * t[k].a * cs;
-            gi = C * t[k].a * sn;
-            float ur = A * cs, ui = -A * sn;
-            v[0] = ur; v[1] = ui;
-            v[2] = cgm * ur + sgm * ui; v[3] = cgm * ui - sgm * ur;   // conj(kappa) u
-            v[4] = cgm * ur - sgm * ui; v[5] = cgm * ui + sgm * ur;   // kappa u
+            for (int m = 0; m < 6; m++) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v[m]);
+                sv[m][tx][q] = h;
+                if (SPLIT) sv[6 + m][tx][q] = __float2bfloat16_rn(v[m] - __bfloat162float(h));
+            }
+            if (FWD && e0 + q < N && xin) {
+                // G and G v at [e][x], as k_synth_fwd_tc
+                const size_t o = (size_t)(e0 + q) * Xpad + x;
+                __nv_bfloat16 *lo = SPLIT ? fplanes + 4 * fpstride : nullptr;
+                put_split(fplanes + o, SPLIT ? lo + o : nullptr, gr);
+                put_split(fplanes + fpstride + o, SPLIT ? lo + fpstride + o : nullptr, gi);
+                put_split(fplanes + 2 * fpstride + o, SPLIT ? lo + 2 * fpstride + o : nullptr, gv_re(gr, gi, vv));
+                put_split(fplanes + 3 * fpstride + o, SPLIT ? lo + 3 * fpstride + o : nullptr, gv_im(gr, gi, vv));
+            }
         }
-        // the tile transposed to [x][e] in shared memory, already rounded to BF16 (hi, lo)
+        __syncthreads();   // the tile is in sv, and buffer b is free for the tile after next
+        // write-out: two neighbouring transducers per 32-bit store (Npad, e0 and the planes'
+        // base are even, so every store is aligned); entries past the last transducer are
+        // zero, as the padding must be
+        const uint32_t *sw = reinterpret_cast<const uint32_t *>(&sv[0][0][0]);
 #pragma unroll
-        for (int m = 0; m < 6; m++) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(v[m]);
-            sv[m][tx][q] = h;
-            if (SPLIT) sv[6 + m][tx][q] = __float2bfloat16_rn(v[m] - __bfloat162float(h));
-        }
-        if (FWD && e0 + q < N && x < X) {
-            // G and G v at [e][x], as k_synth_fwd_tc
-            const size_t o = (size_t)(e0 + q) * Xpad + x;
-            __nv_bfloat16 *lo = SPLIT ? fplanes + 4 * fpstride : nullptr;
-            put_split(fplanes + o, SPLIT ? lo + o : nullptr, gr);
-            put_split(fplanes + fpstride + o, SPLIT ? lo + fpstride + o : nullptr, gi);
-            put_split(fplanes + 2 * fpstride + o, SPLIT ? lo + 2 * fpstride + o : nullptr, gv_re(gr, gi, vv));
-            put_split(fplanes + 3 * fpstride + o, SPLIT ? lo + 3 * fpstride + o : nullptr, gv_im(gr, gi, vv));
-        }
-    }
-    __syncthreads();
-    // write-out: two neighbouring transducers per 32-bit store (Npad, e0 and the planes' base
-    // are even, so every store is aligned); entries past the last transducer are zero, as the
-    // padding must be
-    const uint32_t *sw = reinterpret_cast<const uint32_t *>(&sv[0][0][0]);
+        for (int j = 0; j < 2; j++) {
+            const int item = threadIdx.x + 256 * j, xr = item >> 4, pr = item & 15;
+            if (x0 + xr < X) {
+                const size_t o = (size_t)(x0 + xr) * Npad + e0 + 2 * pr;
 #pragma unroll
-    for (int j = 0; j < 2; j++) {
-        const int item = threadIdx.x + 256 * j, xr = item >> 4, pr = item & 15;
-        if (x0 + xr < X) {
-            const size_t o = (size_t)(x0 + xr) * Npad + e0 + 2 * pr;
-#pragma unroll
-            for (int m = 0; m < NPL; m++)
-                *reinterpret_cast<uint32_t *>(planes + m * pstride + o) = sw[(m * 32 + xr) * 17 + pr];
+                for (int m = 0; m < NPL; m++)
+                    *reinterpret_cast<uint32_t *>(planes + m * pstride + o) = sw[(m * 32 + xr) * 17 + pr];
+            }
         }
     }
+    cp_async_wait0();
 }
 
 // R_s (complex N x N) -> planes [2][Npad][Npad] (then 2 lo planes when split)
@@ -1006,32 +1026,51 @@ int launch_forward_tc(TcPlanes &p, float2 *part, cudaStream_t s)
     return p.fwd_splits;
 }
 
+// Shared memory and persistent grid of k_synth_tc<FWD, SPLIT> (set up once per instance).
+template <bool FWD, bool SPLIT>
+static int synth_grid(size_t &smem)
+{
+    smem = 2 * kSynSlots * sizeof(TabEntry) + (SPLIT ? 12 : 6) * 32 * 34 * sizeof(__nv_bfloat16);
+    static int blocks = 0;
+    if (blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_synth_tc<FWD, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_synth_tc<FWD, SPLIT>, 256, smem);
+        blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    return blocks;
+}
+
+template <bool FWD, bool SPLIT>
+static void synth_launch(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s)
+{
+    const float fhi = (float)f, flo = (float)(f - (double)fhi);
+    const int XT = (p.X + 31) / 32, ntiles = XT * ((p.N + 31) / 32);
+    size_t smem = 0;
+    int grd = synth_grid<FWD, SPLIT>(smem);
+    if (grd > ntiles) grd = ntiles;
+    k_synth_tc<FWD, SPLIT><<<grd, 256, smem, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, green_const_tc(f, c0),
+                                                  static_cast<__nv_bfloat16 *>(p.bplanes), v, FWD ? p.Xpad : 0,
+                                                  FWD ? p.fwd_pstride : 0,
+                                                  FWD ? static_cast<__nv_bfloat16 *>(p.fplanes) : nullptr, XT, ntiles);
+}
+
 void launch_synth_bp_tc(TcPlanes &p, const TabEntry *tab, double f, double c0, cudaStream_t s)
 {
-    float fhi = (float)f, flo = (float)(f - (double)fhi);
-    dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
-    __nv_bfloat16 *bp = static_cast<__nv_bfloat16 *>(p.bplanes);
-    const float C = green_const_tc(f, c0);
     if (p.split)
-        k_synth_tc<false, true><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, nullptr, 0, 0,
-                                                   nullptr);
+        synth_launch<false, true>(p, tab, nullptr, f, c0, s);
     else
-        k_synth_tc<false, false><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, nullptr, 0,
-                                                    0, nullptr);
+        synth_launch<false, false>(p, tab, nullptr, f, c0, s);
 }
 
 void launch_synth_both_tc(TcPlanes &p, const TabEntry *tab, const float2 *v, double f, double c0, cudaStream_t s)
 {
-    float fhi = (float)f, flo = (float)(f - (double)fhi);
-    dim3 grd((p.X + 31) / 32, (p.N + 31) / 32);
-    __nv_bfloat16 *bp = static_cast<__nv_bfloat16 *>(p.bplanes), *fp = static_cast<__nv_bfloat16 *>(p.fplanes);
-    const float C = green_const_tc(f, c0);
     if (p.split)
-        k_synth_tc<true, true><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, v, p.Xpad,
-                                                  p.fwd_pstride, fp);
+        synth_launch<true, true>(p, tab, v, f, c0, s);
     else
-        k_synth_tc<true, false><<<grd, 256, 0, s>>>(tab, p.N, p.X, p.Npad, p.bp_pstride, fhi, flo, C, bp, v, p.Xpad,
-                                                   p.fwd_pstride, fp);
+        synth_launch<true, false>(p, tab, v, f, c0, s);
 }
 
 // One thread waits, with the bound every tensor-core kernel uses, on an mbarrier that nothing
