@@ -80,6 +80,23 @@ __global__ void k_smooth_x(const float *__restrict__ c, double *__restrict__ t, 
     t[iy * nx + ix] = s / w;
 }
 
+// The same average with the block's row segment and its halo inverted once into shared
+// memory (FP64 division is slow on this part: one per node instead of w), summed in the same
+// order, so the result is the same bit for bit.
+__global__ void k_smooth_x_inv(const float *__restrict__ c, double *__restrict__ t, int nx, int ny, int w)
+{
+    extern __shared__ double rinv[];   // [blockDim.x + w - 1]
+    const int h = (w - 1) / 2, ix0 = blockIdx.x * blockDim.x, iy = blockIdx.y;
+    for (int q = threadIdx.x; q < (int)blockDim.x + 2 * h; q += blockDim.x)
+        rinv[q] = 1.0 / (double)c[iy * nx + clampi(ix0 - h + q, 0, nx - 1)];
+    __syncthreads();
+    const int ix = ix0 + threadIdx.x;
+    if (ix >= nx) return;
+    double s = 0;
+    for (int d = -h; d <= h; d++) s += rinv[threadIdx.x + h + d];
+    t[iy * nx + ix] = s / w;
+}
+
 // Moving average along y (edges replicated).
 __global__ void k_smooth_y(const double *__restrict__ t, double *__restrict__ ns64, float *__restrict__ ns, int nx,
                            int ny, int w)
@@ -156,7 +173,11 @@ void launch_smooth_fields(const rbx_geometry &g, const float *c, int w, double *
                           float *fields, const Lossy &ab, double f, bool raw, cudaStream_t s)
 {
     dim3 blk(128), grd((g.nx + 127) / 128, g.ny);
-    k_smooth_x<<<grd, blk, 0, s>>>(c, tmp64, g.nx, g.ny, w);
+    const size_t inv_smem = (size_t)(128 + w - 1) * sizeof(double);
+    if (inv_smem <= 32768)
+        k_smooth_x_inv<<<grd, blk, inv_smem, s>>>(c, tmp64, g.nx, g.ny, w);
+    else   // a window over 4000 nodes: invert in the sum
+        k_smooth_x<<<grd, blk, 0, s>>>(c, tmp64, g.nx, g.ny, w);
     k_smooth_y<<<grd, blk, 0, s>>>(tmp64, ns64, ns, g.nx, g.ny, w);
     double tn = 0.0, wy = 0.0;
     if (ab.alpha0) {

@@ -616,22 +616,26 @@ __global__ __launch_bounds__(32 * kFansPerBlock, 20 / kFansPerBlock) void k_trac
 __global__ void k_uniform_radius(const float4 *__restrict__ F, RayParams p, unsigned long long *ru)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= p.nx * p.ny) return;
-    const size_t nxy = (size_t)p.nx * p.ny;
-    const float2 *F2 = reinterpret_cast<const float2 *>(F + nxy), *F3 = F2 + nxy;
-    const float4 u0 = F[0], a0 = F[k];
-    const float2 v0 = F2[0], v1 = F3[0], b0 = F2[k], b1 = F3[k];
-    const float4 u1 = make_float4(v0.x, v0.y, v1.x, v1.y), a1 = make_float4(b0.x, b0.y, b1.x, b1.y);
-    if (k == 0 && !(u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && u1.x == 0.f && u1.y == 0.f)) {
-        atomicMax(ru, (unsigned long long)__float_as_uint(__int_as_float(0x7f800000)));
-        return;
+    unsigned r = 0u;   // bits of a non-negative float: their order is the values' order
+    if (k < p.nx * p.ny) {
+        const size_t nxy = (size_t)p.nx * p.ny;
+        const float2 *F2 = reinterpret_cast<const float2 *>(F + nxy), *F3 = F2 + nxy;
+        const float4 u0 = F[0], a0 = F[k];
+        const float2 v0 = F2[0], v1 = F3[0], b0 = F2[k], b1 = F3[k];
+        const float4 u1 = make_float4(v0.x, v0.y, v1.x, v1.y), a1 = make_float4(b0.x, b0.y, b1.x, b1.y);
+        if (k == 0 && !(u0.y == 0.f && u0.z == 0.f && u0.w == 0.f && u1.x == 0.f && u1.y == 0.f)) {
+            r = 0x7f800000u;   // +inf
+        } else {
+            const bool uni = a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f &&
+                             a1.y == 0.f && a1.z == u1.z && a1.w == u1.w;
+            if (!uni) {
+                const float px = p.x0 + (float)(k % p.nx) * p.dx, py = p.y0 + (float)(k / p.nx) * p.dx;
+                r = __float_as_uint(sqrtf(px * px + py * py));
+            }
+        }
     }
-    const bool uni = a0.x == u0.x && a0.y == 0.f && a0.z == 0.f && a0.w == 0.f && a1.x == 0.f && a1.y == 0.f &&
-                     a1.z == u1.z && a1.w == u1.w;
-    if (!uni) {
-        const float px = p.x0 + (float)(k % p.nx) * p.dx, py = p.y0 + (float)(k / p.nx) * p.dx;
-        atomicMax(ru, (unsigned long long)__float_as_uint(sqrtf(px * px + py * py)));
-    }
+    r = __reduce_max_sync(0xffffffffu, r);   // one atomic per warp
+    if ((threadIdx.x & 31) == 0 && r) atomicMax(ru, (unsigned long long)r);
 }
 
 void launch_uniform_radius(const float *fields, const RayParams &p, unsigned long long *ru, cudaStream_t s)
