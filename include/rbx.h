@@ -217,9 +217,12 @@ rbx_status rbx_update_frequency(rbx_job *job, double freq_hz, double dfreq_hz, c
  * recomputed from the current model with the window of freq_hz. */
 rbx_status rbx_update_from_tables(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_dev, rbx_stats *out);
 
-/* As rbx_update_frequency with host buffers: copies data_host (N x N complex64) to the
- * device, runs the update and copies the updated model to c_out_host (ny*nx float32,
- * may be NULL). */
+/* As rbx_update_frequency with host buffers: copies data_host (N x N complex64; pinned
+ * memory for an asynchronous copy) to the device on a copy stream of the job, beside the ray
+ * trace, which does not read the data; runs the update and copies the updated model to
+ * c_out_host (ny*nx float32, may be NULL), one wait for the model and the statistics. The
+ * results are those of rbx_update_frequency, bit for bit. On RBX_ENUMERIC c_out_host holds
+ * the model as kept (previous values at the failing nodes). */
 rbx_status rbx_update_frequency_host(rbx_job *job, double freq_hz, double dfreq_hz, const void *data_host,
                                      float *c_out_host, rbx_stats *out);
 

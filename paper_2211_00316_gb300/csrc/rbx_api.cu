@@ -40,6 +40,9 @@ struct rbx_job {
     cudaEvent_t *slot_ev = nullptr;     // [kHistSlots][EV_COUNT] (rbx_set_slot_timing)
     long long slot_launches[kHistSlots] = {};
     long long slot_l0 = 0;     // launch count when the update being queued began
+    // rbx_update_frequency_host: a copy stream for the data, which the trace does not read
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_in_free = nullptr, ev_in_ready = nullptr;
     long long launches = 0;
 };
 
@@ -161,6 +164,12 @@ rbx_status rbx_destroy(rbx_job *j)
     cudaStreamSynchronize(j->stream);
     for (int k = 0; k < EV_COUNT; k++)
         if (j->ev[k]) cudaEventDestroy(j->ev[k]);
+    if (j->copy_stream) {
+        cudaStreamSynchronize(j->copy_stream);
+        cudaStreamDestroy(j->copy_stream);
+    }
+    if (j->ev_in_free) cudaEventDestroy(j->ev_in_free);
+    if (j->ev_in_ready) cudaEventDestroy(j->ev_in_ready);
     if (j->slot_ev) {
         for (int k = 0; k < kHistSlots * EV_COUNT; k++)
             if (j->slot_ev[k]) cudaEventDestroy(j->slot_ev[k]);
@@ -886,16 +895,38 @@ rbx_status rbx_update_frequency_host(rbx_job *j, double f, double df, const void
 {
     if (!j || !data_host) return RBX_EINVAL;
     NEED(j, j->has_geom, RBX_ESTATE, "rbx_update_frequency_host before rbx_set_geometry");
+    NEED(j, !bad_freq(f) && std::isfinite(df) && df > 0, RBX_EINVAL, "frequency and spacing must be finite and > 0");
+    if (!j->copy_stream) {
+        CUDA_TRY(j, cudaStreamCreateWithFlags(&j->copy_stream, cudaStreamNonBlocking));
+        CUDA_TRY(j, cudaEventCreateWithFlags(&j->ev_in_free, cudaEventDisableTiming));
+        CUDA_TRY(j, cudaEventCreateWithFlags(&j->ev_in_ready, cudaEventDisableTiming));
+    }
+    // The data's copy runs on the copy stream beside the trace (which does not read it), after
+    // the work already queued on the job's stream, which may still read the previous data.
     size_t nn = (size_t)j->w.N * j->w.N;
-    CUDA_TRY(j, cudaMemcpyAsync(j->w.data, data_host, sizeof(float2) * nn, cudaMemcpyHostToDevice, j->stream));
-    rbx_status st = rbx_update_frequency(j, f, df, j->w.data, out);
-    if (st) return st;
-    if (c_out_host) {
+    CUDA_TRY(j, cudaEventRecord(j->ev_in_free, j->stream));
+    CUDA_TRY(j, cudaStreamWaitEvent(j->copy_stream, j->ev_in_free, 0));
+    CUDA_TRY(j, cudaMemcpyAsync(j->w.data, data_host, sizeof(float2) * nn, cudaMemcpyHostToDevice, j->copy_stream));
+    CUDA_TRY(j, cudaEventRecord(j->ev_in_ready, j->copy_stream));
+    const long long l0 = j->launches;
+    rbx_status st = rbx_trace_rays(j, f);
+    if (st) {
+        cudaStreamSynchronize(j->copy_stream);   // the copy still reads data_host
+        return st;
+    }
+    CUDA_TRY(j, cudaStreamWaitEvent(j->stream, j->ev_in_ready, 0));
+    st = enqueue_update(j, f, df, j->w.data, true, 0);
+    if (st) {
+        cudaStreamSynchronize(j->stream);
+        return st;
+    }
+    if (c_out_host) {   // queued before the statistics' read, so that one wait covers both
         size_t nxy = (size_t)j->w.nx * j->w.ny;
         CUDA_TRY(j, cudaMemcpyAsync(c_out_host, j->w.c, sizeof(float) * nxy, cudaMemcpyDeviceToHost, j->stream));
-        CUDA_TRY(j, cudaStreamSynchronize(j->stream));
     }
-    return RBX_OK;
+    st = read_stats(j, 0, out, true, true);
+    if (out) out->n_launches = j->launches - l0;
+    return st;
 }
 
 // rbx_update_frequency_async in two halves around the ray trace's launch (the batched form's
