@@ -817,7 +817,8 @@ __global__ void k_direct_green(const float4 *__restrict__ exits, int N, const do
 {
     extern __shared__ float4 ex[];
     double *reld = reinterpret_cast<double *>(ex + (N - 1));   // receiver angle relative to beta_e by ring place
-    float *th = reinterpret_cast<float *>(reld + N);           // exit angle relative to beta_e, in [0, 2 pi)
+    double *thd = reld + N;                                    // exit angle relative to beta_e, in [0, 2 pi)
+    float *th = reinterpret_cast<float *>(thd + (N - 1));      // thd rounded to float
     float *relt = th + (N - 1);                                // reld rounded to float
     int *first = reinterpret_cast<int *>(relt + N);            // first bracketing pair per receiver
     const int e = blockIdx.x;
@@ -825,7 +826,8 @@ __global__ void k_direct_green(const float4 *__restrict__ exits, int N, const do
     for (int q = threadIdx.x; q < N - 1; q += blockDim.x) {
         float4 v = exits[(size_t)e * (N - 1) + q];
         ex[q] = v;
-        th[q] = (float)wrap_turn((double)v.x - be);
+        thd[q] = wrap_turn((double)v.x - be);
+        th[q] = (float)thd[q];
     }
     for (int m = threadIdx.x; m < N; m += blockDim.x) {
         reld[m] = recv_rel_m(m, e, N, step, beta, be);
@@ -844,7 +846,7 @@ __global__ void k_direct_green(const float4 *__restrict__ exits, int N, const do
         if (found > 0) {
             float4 A = ex[found - 1], B = ex[found];
             // the bracket fraction from the exit angles in double precision
-            const double ta = wrap_turn((double)A.x - be), tb = wrap_turn((double)B.x - be);
+            const double ta = thd[found - 1], tb = thd[found];
             const double fr = (td - ta) / (tb - ta);
             T = (float)((double)A.y + fr * ((double)B.y - (double)A.y));
             a = (float)((double)A.z + fr * ((double)B.z - (double)A.z));
@@ -871,10 +873,10 @@ void launch_direct_green(const float4 *exits, int N, const double *beta, double 
 {
     float fhi = (float)f, flo = (float)(f - (double)fhi);
     float C = (float)(1.0 / sqrt(8.0 * 3.14159265358979323846 * (2.0 * 3.14159265358979323846 * f) / c0));
-    size_t smem = (size_t)(N - 1) * (sizeof(float4) + sizeof(float)) +
-                  (size_t)N * (sizeof(double) + sizeof(float) + sizeof(int));   // <= 147 KB at N = 4095
+    size_t smem = (size_t)(N - 1) * (sizeof(float4) + sizeof(double) + sizeof(float)) +
+                  (size_t)N * (sizeof(double) + sizeof(float) + sizeof(int));   // <= 180 KB at N = 4095
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_direct_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_direct_green<<<N, 256, smem, s>>>(exits, N, beta, fhi, flo, C, g, counters);
+    k_direct_green<<<N, 512, smem, s>>>(exits, N, beta, fhi, flo, C, g, counters);
 }
 
 // ---------------------------------------------------------------- ray linking
