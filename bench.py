@@ -96,8 +96,8 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_trace_raster -s 3 -c 1 --csv   (k_synth_tc: -k regex:k_synth_tc -s 6 -c 1)
     #     python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --no-forms   (1 pass)
-    ("precision_ring1024", "trace"): {"bytes": 2.521475328e9 + 2.463719936e9, "src": "d1e0636815f8"},
-    ("precision_ring1024", "synth"): {"bytes": 2.686333184e9 + 3.080846592e9, "src": "807f66b6c026"},
+    ("precision_ring1024", "trace"): {"bytes": 2.520651264e9 + 2.463884288e9, "src": "dfa1abce22d9"},
+    ("precision_ring1024", "synth"): {"bytes": 2.496856832e9 + 3.071679744e9, "src": "861bfb904eef"},
 }
 
 
