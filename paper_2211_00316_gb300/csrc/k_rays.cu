@@ -340,8 +340,12 @@ __device__ __forceinline__ void trace_block(const float *__restrict__ F, const i
     field_eval<LOSSY, RAW>(F, p, x, y, F1);
     float px, py, dpx, dpy, dxx = 0.f, dxy = 0.f, T = 0.f, Tc = 0.f;
     float B = 0.f, Bc = 0.f;   // lossy media: B = int alpha ds by the rule of T; a gains exp(-B)
-    // compensation terms of x, p, dx (T has Tc)
-    float cx = 0.f, cy = 0.f, cpx = 0.f, cpy = 0.f, cdx = 0.f, cdy = 0.f;
+    // compensation terms of the position and of the paraxial ray's closed-form steps (T has
+    // Tc). In the Heun steps the momentum, renormalised to n(x) at every step, and the
+    // paraxial ray, which only sets the amplitude, take plain sums: compensated too, the
+    // tables met the same parity bars against the FP64 oracle (T 1e-9 s, a 1e-5) and the
+    // trace took 1.6 % longer.
+    float cx = 0.f, cy = 0.f, cdx = 0.f, cdy = 0.f;
 
     // Uniform water near the ring (exact up to rounding). Beyond radius rho every cell that a
     // sample or an auxiliary point can touch holds the same medium with zero derivatives (rho
@@ -396,7 +400,6 @@ __device__ __forceinline__ void trace_block(const float *__restrict__ F, const i
             const float n = F1.n, in = rcp_nr(n);
             const float sc = n * rsqrtf(px * px + py * py);
             px *= sc; py *= sc;
-            cpx *= sc; cpy *= sc;
             const float qx = px * in, qy = py * in;
             // stage 2 at the auxiliary point x + ds q_x
             Fv F2;
@@ -448,8 +451,8 @@ __device__ __forceinline__ void trace_block(const float *__restrict__ F, const i
                 field_eval<LOSSY, RAW>(F, p, x, y, F2);
             } else {
                 kadd(x, cx, ds * dirx); kadd(y, cy, ds * diry);
-                kadd(px, cpx, ddpx); kadd(py, cpy, ddpy);
-                kadd(dxx, cdx, ddxx); kadd(dxy, cdy, ddxy);
+                px += ddpx; py += ddpy;
+                dxx += ddxx; dxy += ddxy;
                 dpx += ddpx2; dpy += ddpy2;
             }
             kadd(T, Tc, inc);   // trapezoid of n along the samples
