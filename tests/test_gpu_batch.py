@@ -113,6 +113,29 @@ def test_grouped_more_jobs_than_one_launch():
         j.close()
 
 
+def test_grouped_ignored_for_mixed_media():
+    """A batch whose jobs differ in their absorption setting has no single trace kernel for
+    all of them: the grouped flag is then ignored and the models equal those of the jobs run
+    one after the other, bit for bit."""
+    ws = slices()
+    jobs, data = prepare(ws, rbx.RBX_BF16)
+    w1 = ws[1]
+    a0 = torch.tensor(P.absorption_map(w1.c_true).astype(np.float32), device="cuda")
+    jobs[1].set_absorption(a0, 1.4)
+    seq = []
+    for w, j, d in zip(ws, jobs, data):
+        j.set_model(torch.tensor(w.c_init, dtype=torch.float32, device="cuda"))
+        j.reconstruct(w.freqs, d)
+        seq.append(j.get_model().cpu().numpy())
+    for w, j in zip(ws, jobs):
+        j.set_model(torch.tensor(w.c_init, dtype=torch.float32, device="cuda"))
+    rbx.batch_run(jobs, [w.freqs for w in ws], data, use_graph=True, grouped=True)
+    for k, j in enumerate(jobs):
+        np.testing.assert_array_equal(j.get_model().cpu().numpy(), seq[k])
+    for j in jobs:
+        j.close()
+
+
 def test_grouped_tables_match_per_job():
     """The tables of one grouped trace equal the per-job trace's within the oracle parity
     tolerances (T 1e-9 s, a 1e-5 relative, gamma 1e-5 rad, exits), K and coverage exactly."""
