@@ -256,10 +256,12 @@ rbx_status rbx_set_slot_timing(rbx_job *job, int on);
  * integration settings, and is ignored otherwise. Without it, results are the same, bit for
  * bit, as running the jobs one after the other; with it, the grouped trace is a separate
  * compilation of the same arithmetic, whose tables agree with the per-job trace's to
- * rounding (travel times within 1e-11 s, amplitudes within 5e-6 relative; coverage and
- * caustic counts the same), and it is deterministic itself. last[i] (nullable) receives job
- * i's last update's scalars; ms_total (nullable) the device time of the whole batch. The
- * jobs' own streams are drained first and kept. */
+ * rounding (the same coverage, travel times within 1e-10 s, amplitudes within 2e-5
+ * relative but at near-caustic entries, where the amplitude is ill-conditioned, and the
+ * caustic count of an entry at most rarely different), and it is deterministic itself. A
+ * whole sweep carries that difference into the models as it carries the BF16 / FP32 one.
+ * last[i] (nullable) receives job i's last update's scalars; ms_total (nullable) the device
+ * time of the whole batch. The jobs' own streams are drained first and kept. */
 #define RBX_BATCH_GRAPH 1
 #define RBX_BATCH_GROUPED 2
 rbx_status rbx_batch_run(rbx_job *const *jobs, int n, const double *const *freqs, const int *nf,
