@@ -894,8 +894,9 @@ void launch_direct_green(const float4 *exits, int N, const double *beta, double 
 // ---------------------------------------------------------------- ray linking
 
 // One ray from (x, y) to the ring by one thread: the Heun and paraxial step of k_trace_raster
-// (same normalisations, compensated sums and final partial step) without its rasterisation
-// and straight-line shortcuts. The initial direction is formed in double so that a secant
+// (same normalisations, the same compensated sums of the position and T and plain sums of
+// the momentum and the paraxial ray, the same reciprocals, the same final partial step)
+// without its rasterisation and straight-line shortcuts. The initial direction is formed in double so that a secant
 // iteration on it is not limited by FP32 rounding of the angle. Returns false when the ray
 // does not reach the ring within p.maxs steps.
 template <bool LOSSY, bool RAW>
@@ -909,18 +910,17 @@ __device__ bool trace_one(const float *__restrict__ F, const RayParams &p, float
     sincos(gam0, &sd, &cd);
     float px = F1.n * (float)cd, py = F1.n * (float)sd, dpx = -F1.n * (float)sd, dpy = F1.n * (float)cd;
     float dxx = 0.f, dxy = 0.f, T = 0.f, Tc = 0.f, B = 0.f, Bc = 0.f;
-    float cx = 0.f, cy = 0.f, cpx = 0.f, cpy = 0.f, cdx = 0.f, cdy = 0.f;
+    float cx = 0.f, cy = 0.f;
     float sc1 = 0.f, Jlast = 0.f;
     int K = 0;
     for (int i = 0; i < p.maxs; i++) {
-        const float n = F1.n, in = rcp_nr(n);
+        const float n = F1.n, in = rcp_ap(n);
         const float sc = n * rsqrtf(px * px + py * py);
         px *= sc; py *= sc;
-        cpx *= sc; cpy *= sc;
         const float qx = px * in, qy = py * in;
         Fv F2;
         field_eval<LOSSY, RAW>(F, p, x + ds * qx, y + ds * qy, F2);
-        const float na = F2.n, ina = rcp_nr(na);
+        const float na = F2.n, ina = rcp_ap(na);
         float pax = px + ds * F1.gx, pay = py + ds * F1.gy;
         const float sca = na * rsqrtf(pax * pax + pay * pay);
         pax *= sca; pay *= sca;
@@ -962,8 +962,8 @@ __device__ bool trace_one(const float *__restrict__ F, const RayParams &p, float
             field_eval<LOSSY, RAW>(F, p, x, y, F2);
         } else {
             kadd(x, cx, ds * dirx); kadd(y, cy, ds * diry);
-            kadd(px, cpx, ddpx); kadd(py, cpy, ddpy);
-            kadd(dxx, cdx, ddxx); kadd(dxy, cdy, ddxy);
+            px += ddpx; py += ddpy;
+            dxx += ddxx; dxy += ddxy;
             dpx += ddpx2; dpy += ddpy2;
         }
         kadd(T, Tc, inc);
