@@ -96,7 +96,7 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_trace_raster -s 3 -c 1 --csv   (k_synth_tc: -k regex:k_synth_tc -s 6 -c 1)
     #     python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --no-forms   (1 pass)
-    ("precision_ring1024", "trace"): {"bytes": 2.520723968e9 + 2.463476992e9, "src": "f34d3f12983d"},
+    ("precision_ring1024", "trace"): {"bytes": 2.521059840e9 + 2.463850752e9, "src": "40dc5317b6bf"},
     ("precision_ring1024", "synth"): {"bytes": 2.496856832e9 + 3.071679744e9, "src": "861bfb904eef"},
 }
 
